@@ -1,0 +1,232 @@
+/*
+ * fio.h -- C ABI of the GB300 (sm_103a) library that applies discrete Fourier
+ * integral operators with the wedge-factorised algorithm of Candes, Demanet and
+ * Ying, "Fast Computation of Fourier Integral Operators".
+ *
+ * The operator (Sec. 1.2, Eq. dfio with the unitary DFT of Eq. dft):
+ *
+ *     (Lf)(x) = (1/N) sum_{xi in Omega} a(x,xi) exp(2 pi i Phi(x,xi)) fhat(xi),
+ *     fhat(xi) = (1/N) sum_{x in X} exp(-2 pi i x.xi) f(x),
+ *
+ * on X = {(n1/N, n2/N) : 0 <= n1, n2 < N} and Omega = [-N/2, N/2)^2 (N even).
+ *
+ * Data layout shared by every call:
+ *   - an N x N grid function is N*N interleaved complex numbers (re, im),
+ *     index n1*N + n2 holds the value at x = (n1/N, n2/N);
+ *   - a batch of B grid functions is B such arrays back to back;
+ *   - precision FIO_MIXED uses complex64 (two floats), FIO_FP64 complex128;
+ *   - a spectrum (fio_dft2) is in centred order: index (k1 + N/2)*N + (k2 + N/2)
+ *     holds xi = (k1, k2).
+ *
+ * Pointers named f, g, out, in are DEVICE pointers owned by the caller.  The
+ * plan owns its own device memory.  `stream` is a cudaStream_t (NULL = the
+ * legacy default stream); every apply call is asynchronous on it and does no
+ * host synchronisation.
+ *
+ * Errors: every call returns a status code and never throws.  A CUDA error from
+ * an asynchronous launch is reported by that call if the launch fails, or by a
+ * later call (fio_plan_sync).  fio_last_error() returns a thread-local message
+ * describing the last failure of the calling thread.
+ */
+#ifndef FIO_H_
+#define FIO_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct fio_plan_s *fio_plan;
+
+typedef enum {
+  FIO_OK = 0,
+  FIO_EINVAL = 1,        /* invalid argument (N odd or out of range, eps, NaN params, ...) */
+  FIO_ENOMEM = 2,        /* a device or host allocation failed; nothing leaks */
+  FIO_ECUDA = 3,         /* a CUDA runtime call or kernel launch failed */
+  FIO_ERANK = 4,         /* the adaptive sample count exceeded rank_cap (Sec. 3.2) */
+  FIO_ETIMEOUT = 5,      /* a bounded device wait gave up */
+  FIO_EUNSUPPORTED = 6   /* valid request this build does not implement */
+} fio_status;
+
+/* Phase functions Phi(x, xi) = x.xi + Psi(x, xi), homogeneous of degree 1 in xi.
+ * theta = arg(xi) = atan2(xi2, xi1); every phase is 0 at xi = 0. */
+typedef enum {
+  /* Psi = -x0.xi + c|xi|; params {x01, x02, c}.  Translation by x0 and the
+   * constant-speed wave propagator of Sec. 1.1 (Eq. wave_solution). */
+  FIO_PHASE_SHIFT_WAVE = 0,
+  /* Psi = sqrt(c1(x)^2 xi1^2 + c2(x)^2 xi2^2) with
+   * c1 = A1 + B1 sin(2 pi x1) sin(2 pi x2), c2 = A2 + B2 cos(2 pi x1) cos(2 pi x2);
+   * params {A1, B1, A2, B2}.  The ellipse phase family of Sec. 4 (Eq. nrphase). */
+  FIO_PHASE_ELLIPSE = 1,
+  /* Psi = |xi| tau(x, theta), tau = sum_j a_j cos(2 pi (k1_j x1 + k2_j x2) + m_j theta + p_j);
+   * params: nmodes rows {a_j, k1_j, k2_j, m_j, p_j}, m_j an integer in [-8, 8]. */
+  FIO_PHASE_TAU_MODES = 2
+} fio_phase_kind;
+
+typedef struct {
+  int kind;              /* fio_phase_kind */
+  int nmodes;            /* FIO_PHASE_TAU_MODES only */
+  const double *params;  /* HOST memory, read during fio_plan_create only */
+} fio_phase;
+
+typedef enum {
+  FIO_AMP_ONE = 0,       /* a = 1 (the Egorov operator of Sec. 3) */
+  FIO_AMP_SEPARABLE = 1  /* a = (1 + a1 sin 2 pi x1)(1 + a2 cos theta), cos theta := 1 at xi = 0 */
+} fio_amp_kind;
+
+typedef struct {
+  int kind;              /* fio_amp_kind */
+  double a1, a2;
+} fio_amplitude;
+
+typedef enum {
+  FIO_MIXED = 0,  /* complex64 FFT / NUFFT / accumulation; FP64 plan */
+  FIO_FP64 = 1    /* complex128 everywhere */
+} fio_precision;
+
+typedef struct {
+  int precision;              /* fio_precision (default FIO_MIXED) */
+  int L;                      /* number of wedges; 0 = ceil(sqrt(N)) rounded up to a multiple of 8 */
+  double sigma;               /* NUFFT oversampling factor; 0 = 2 */
+  int kb_width;               /* Kaiser-Bessel width in grid cells; 0 = ceil(log10(45/eps)) */
+  unsigned long long seed;    /* seed of the random column/row samples of Sec. 3.2 */
+  int r0;                     /* initial sample count r; 0 = 8 */
+  int rank_cap;               /* largest r before FIO_ERANK; 0 = 512 */
+  int max_batch;              /* largest batch the plan's workspace holds; 0 = 1 */
+} fio_options;
+
+/* Fill *opt with the defaults listed above.  Returns FIO_EINVAL for NULL. */
+fio_status fio_options_default(fio_options *opt);
+
+/* Build a plan for L on an N x N grid (Sec. 1.3 wedges; Sec. 3.2 randomized
+ * separation of a(x,xi) exp(2 pi i Phi_l(x,xi)) to relative accuracy eps; Sec. 3.4
+ * shear/translate boxes and NUFFT grids).
+ *   N      even, 8 <= N <= 2048
+ *   phase  host descriptor, copied; NaN or Inf parameters give FIO_EINVAL
+ *   amp    NULL means a = 1
+ *   eps    separation threshold, 1e-12 <= eps <= 0.1 (singular values below
+ *          eps * s_1 are dropped)
+ *   opt    NULL means defaults
+ * Uses the current CUDA device; synchronises it.  On failure *out_plan = NULL and
+ * every allocation made so far is released. */
+fio_status fio_plan_create(int N, const fio_phase *phase, const fio_amplitude *amp, double eps,
+                           const fio_options *opt, fio_plan *out_plan);
+
+/* out = L f for `batch` inputs (Sec. 3.4 evaluation: FFT, windowed scatter by
+ * gamma^xi, type-2 NUFFT at the warped points, gamma^x multiply and sum).
+ * f, out: device arrays of batch*N*N complex (complex64 for FIO_MIXED plans,
+ * complex128 for FIO_FP64).  1 <= batch <= max_batch.  out must not alias f.
+ * One plan must not be used on two streams at the same time (shared workspace). */
+fio_status fio_apply(fio_plan plan, const void *f, void *out, int batch, void *stream);
+
+/* out = L* g (Sec. 3.5: gamma^x-conjugate multiply, type-1 NUFFT, conj(gamma^xi)
+ * windowed gather, inverse FFT).  Same layout and rules as fio_apply.  The result
+ * is the exact conjugate transpose of the fast forward operator, so
+ * <L f, g> = <f, L* g> holds to rounding. */
+fio_status fio_apply_adjoint(fio_plan plan, const void *g, void *out, int batch, void *stream);
+
+/* Wait for the plan's work on `stream` and report any pending CUDA error. */
+fio_status fio_plan_sync(fio_plan plan, void *stream);
+
+typedef struct {
+  int N, L, precision, kb_width, max_batch;
+  double sigma, kb_beta, eps;
+  int q_max, q_min, r_max;
+  double q_mean;
+  unsigned long long bytes_alpha;   /* gamma^x factors on the device */
+  unsigned long long bytes_beta;    /* gamma^xi factors */
+  unsigned long long bytes_warp;    /* warped points */
+  unsigned long long bytes_grid;    /* NUFFT grids for max_batch inputs */
+  unsigned long long bytes_total;   /* all device memory the plan holds */
+  unsigned long long grid_points;   /* sum over wedges of m1*m2*q (one input) */
+  unsigned long long alg_bytes_apply; /* algorithmic HBM bytes of one batch-1 apply */
+  double plan_seconds;              /* wall time of fio_plan_create */
+} fio_plan_info;
+
+/* Plan summary (host struct filled). */
+fio_status fio_plan_get_info(fio_plan plan, fio_plan_info *info);
+
+typedef struct {
+  int M[4];          /* shear: xi'' = M xi, row-major integer matrix, det 1 */
+  int xc1, xc2;      /* box centre xi_c: xi' = M xi - xi_c */
+  int b1, n1, b2, n2; /* box: xi'_1 in [b1, b1+n1), xi'_2 in [b2, b2+n2) */
+  int m1, m2;        /* oversampled grid */
+  int q;             /* separation rank */
+  int r;             /* final random sample count */
+  int npts;          /* |W_l|: frequencies owned by this wedge */
+} fio_wedge_info;
+
+/* Geometry and rank of wedge l (0 <= l < L). */
+fio_status fio_plan_get_wedge(fio_plan plan, int l, fio_wedge_info *info);
+
+/* Export the separated factors of wedge l to HOST arrays (complex128):
+ *   alpha[t*N*N + x] = gamma^x_{l t}(x)  (columns of U, Sec. 3.2),
+ *   beta[t*npts + p] = gamma^xi_{l t}(xi_p) (rows of T), with xi_p = (k1[p], k2[p]).
+ * Any pointer may be NULL.  Sizes: alpha q*N*N, beta q*npts, k1/k2 npts.  For tests
+ * of the separation error (the estimator of Sec. 4, Table 1). */
+fio_status fio_plan_export_wedge(fio_plan plan, int l, double *alpha, double *beta, int *k1,
+                                 int *k2);
+
+/* Export the warped points of wedge l as the plan stores them: y[2*x + d] =
+ * (M^-T grad_xi Phi(x, xihat_l))_d mod 1, rounded to 32-bit fractions (HOST
+ * array of 2*N*N doubles).  With the factors of fio_plan_export_wedge,
+ * exp(2 pi i Phi(x,xi)) a(x,xi) ~ exp(2 pi i y(x).(M xi)) sum_t alpha_t(x) beta_t(xi)
+ * for xi in W_l (Sec. 1.4 and Sec. 3.2). */
+fio_status fio_plan_export_warp(fio_plan plan, int l, double *y);
+
+void fio_plan_destroy(fio_plan plan);
+
+/* Unitary 2D DFT of Eq. dft (inverse = 0) or its inverse (inverse = 1) on the
+ * GPU, spectrum in centred order.  in/out: device arrays of batch*N*N complex
+ * (precision as above); in == out is allowed.  N = 2^a 3^b 5^c, 8 <= N <= 4096. */
+fio_status fio_dft2(int N, int precision, const void *in, void *out, int batch, int inverse,
+                    void *stream);
+
+/* ---------------------------------------------------------------------------
+ * Host utilities.  They run on the CPU only (no CUDA call), so the host logic
+ * of the plan can be inspected and tested without a GPU.
+ * ------------------------------------------------------------------------- */
+
+/* Default wedge count for N: ceil(sqrt N) (Sec. 1.3 takes sqrt N wedges)
+ * rounded up to a multiple of 8, so that both diagonals are wedge centres. */
+int fio_default_wedges(int N);
+
+/* wedge_of[(k1 + N/2)*N + (k2 + N/2)] = l with
+ * (2l - 1) pi / L <= arg xi < (2l + 1) pi / L (Sec. 1.3); xi = 0 is put in wedge 0.
+ * wedge_of: host array of N*N ints. */
+fio_status fio_wedge_map(int N, int L, int *wedge_of);
+
+/* Box and grid of wedge l as fio_plan_create builds them (Sec. 3.4), for
+ * oversampling sigma and KB width kb_width (q and r are returned as 0). */
+fio_status fio_wedge_geometry(int N, int L, double sigma, int kb_width, int l,
+                              fio_wedge_info *info);
+
+/* Kaiser-Bessel kernel phi(s) = I0(beta sqrt(1 - (2s/w)^2)) / I0(beta) (0 for
+ * |s| >= w/2) at n points s[], and its Fourier transform
+ * phihat(nu) = int phi(s) exp(-2 pi i nu s) ds at n points nu[] (host arrays;
+ * phi / phihat may be NULL to skip).  beta <= 0 selects the default shape
+ * pi sqrt((w/sigma)^2 (sigma - 1/2)^2 - 0.8) for sigma = 2. */
+fio_status fio_kb_eval(int w, double beta, int n, const double *s, double *phi, const double *nu,
+                       double *phihat);
+
+/* Default KB width for a separation threshold eps: ceil(log10(45 / eps)). */
+int fio_kb_width_for(double eps);
+
+/* Eigendecomposition of a Hermitian n x n complex matrix (host, row-major,
+ * interleaved re/im, n <= 1024) by cyclic Jacobi rotations: evals descending,
+ * V's columns the eigenvectors (row-major interleaved).  This is the solver the
+ * randomized separation uses for the Gram matrix of the sampled columns. */
+fio_status fio_host_eigh(int n, const double *A, double *evals, double *V);
+
+const char *fio_status_string(fio_status s);
+const char *fio_last_error(void);
+
+/* Library version as major*10000 + minor*100 + patch. */
+int fio_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* FIO_H_ */

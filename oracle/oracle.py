@@ -16,6 +16,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 import threading
 
@@ -33,11 +34,16 @@ SHIFT_WAVE, ELLIPSE, TAU_MODES = 0, 1, 2
 
 def build(force: bool = False) -> str:
     """Compile fio_oracle.c into liboracle.so next to it (gcc, -O2, OpenMP)."""
+    stamp = _LIB + ".arch"
+    if not os.path.exists(stamp) or open(stamp).read().strip() != platform.machine():
+        force = True  # built on another machine
     if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-fopenmp", "-fPIC", "-shared", "-std=c11", _SRC,
                                "-o", tmp, "-lm"])
         os.replace(tmp, _LIB)
+        with open(stamp, "w") as fh:
+            fh.write(platform.machine())
     return _LIB
 
 

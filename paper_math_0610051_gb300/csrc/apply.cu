@@ -1,0 +1,571 @@
+// apply.cu -- the evaluation step of the wedge-factorised FIO (Sec. 3.4) and
+// its adjoint (Sec. 3.5), as sm_103a kernels templated on the real type
+// (float: the mixed path, double: the FP64 path).
+//
+// Forward, for each input b:
+//   S0  fhat = unitary 2D DFT of f                                   (Eq. dft)
+//   S1  for every wedge l, rank term t and box row xi'_1: place
+//       beta'_t(xi) fhat(xi) at xi'_2 mod m2 (beta' = gamma^xi / phihat) and
+//       FFT the row (exp(+2 pi i)) -- the "form fhat_{l t}" step
+//   S2  FFT every grid column over the box rows (exp(+2 pi i))
+//   S3  for every x: KB-interpolate each grid G_{l t} at the warped point
+//       u = y'_l(x) m, multiply by alpha'_t(x) (gamma^x with the centre-frequency
+//       factor exp(2 pi i y'.xi_c) and 1/N folded in), sum over t and l.
+// Adjoint: S4a spread conj(alpha') g onto the grids (type-1), S4b forward
+// FFTs (exp(-2 pi i)) with pruned output, S4c sum_t conj(beta') G into the
+// owner wedge's frequencies, S4d inverse unitary DFT.
+//
+// Grid layout: wedge l's grid is [g1 < m1][g2 < m2][ch < B q_l], ch = b q_l + t.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdint>
+
+#include "fft_engine.cuh"
+#include "fio_internal.h"
+
+namespace fio {
+
+template <typename T> using Cx = typename CxT<T>::type;
+
+__device__ __forceinline__ int imodp(int a, int n) {
+  int r = a % n;
+  return r < 0 ? r + n : r;
+}
+
+constexpr int kThreads = 256;
+
+// ------------------------------------------------------------ KB kernel ----
+// phi(s) = I0(beta sqrt(1 - (2s/w)^2)) / I0(beta) for |s| < w/2, else 0.
+__device__ __forceinline__ float kb_phi(float s, float two_over_w, float beta, float inv_i0b) {
+  float z = s * two_over_w;
+  float a = 1.0f - z * z;
+  return a > 0.0f ? cyl_bessel_i0f(beta * sqrtf(a)) * inv_i0b : 0.0f;
+}
+__device__ __forceinline__ double kb_phi(double s, double two_over_w, double beta,
+                                         double inv_i0b) {
+  double z = s * two_over_w;
+  double a = 1.0 - z * z;
+  return a > 0.0 ? cyl_bessel_i0(beta * sqrt(a)) * inv_i0b : 0.0;
+}
+
+struct KbDev {
+  int w;
+  double beta, inv_i0b;
+};
+
+// Decode a 32-bit fraction y' (of one axis) into the first grid cell of the
+// width-w window and the w weights: u = y' m, cells j0..j0+w-1 (mod m),
+// weight phi(u - j).
+template <typename T>
+__device__ __forceinline__ int kb_window(uint32_t Y, int m, const KbDev &kb, T *wgt) {
+  const unsigned long long P = (unsigned long long)Y * (unsigned)m;
+  const int i = (int)(P >> 32);
+  const T f = (T)(uint32_t)P * T(2.3283064365386962890625e-10);  // 2^-32
+  const int hw = kb.w >> 1;
+  int j0 = i - hw + 1;
+  if (kb.w & 1) j0 = i - hw + (f >= T(0.5) ? 1 : 0);
+  const T base = f + T(i - j0);
+  const T tw = T(2.0) / T(kb.w), beta = T(kb.beta), inv = T(kb.inv_i0b);
+  for (int a = 0; a < kb.w; ++a) wgt[a] = kb_phi(base - T(a), tw, beta, inv);
+  return imodp(j0, m);
+}
+
+// --------------------------------------------------------------- S0 / S4d --
+// Unitary 2D DFT passes.  Rows: lines are rows of N contiguous elements.
+// load index (e + load_shift) mod N, store index (e + store_shift) mod N.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_dft_rows(const Cx<T> *in, Cx<T> *out, int N, int nrows, int nl, int sign, int load_shift,
+           int store_shift, FftPlanDev pl, const Cx<T> *tw_g) {
+  using C = Cx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  C *a = reinterpret_cast<C *>(smem_raw);
+  C *b = a + N * nl;
+  C *tw = b + N * nl;
+  const int r0 = blockIdx.x * nl;
+  const int nlc = min(nl, nrows - r0);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    if (tw_g) {
+      tw[k] = tw_g[k];
+    } else {
+      T s, c;
+      if constexpr (sizeof(T) == 4) sincospif(-2.0f * (float)k / (float)N, &s, &c);
+      else sincospi(-2.0 * (double)k / (double)N, &s, &c);
+      tw[k] = C{c, s};
+    }
+  }
+  for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
+    const int e = it % N, l = it / N;
+    a[e * nlc + l] = in[(size_t)(r0 + l) * N + (e + load_shift) % N];
+  }
+  __syncthreads();
+  C *res = fft_exec(a, b, N, nlc, pl, sign, tw);
+  for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
+    const int e = it % N, l = it / N;
+    out[(size_t)(r0 + l) * N + (e + store_shift) % N] = res[e * nlc + l];
+  }
+}
+
+// Columns: lines are nl consecutive columns of one N x N array.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_dft_cols(const Cx<T> *in, Cx<T> *out, int N, int nl, int sign, int load_shift, int store_shift,
+           T scale, FftPlanDev pl, const Cx<T> *tw_g) {
+  using C = Cx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  C *a = reinterpret_cast<C *>(smem_raw);
+  C *b = a + N * nl;
+  C *tw = b + N * nl;
+  const int chunks = (N + nl - 1) / nl;
+  const int bb = blockIdx.x / chunks;
+  const int c0 = (blockIdx.x % chunks) * nl;
+  const int nlc = min(nl, N - c0);
+  const size_t base = (size_t)bb * N * N + c0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    if (tw_g) {
+      tw[k] = tw_g[k];
+    } else {
+      T s, c;
+      if constexpr (sizeof(T) == 4) sincospif(-2.0f * (float)k / (float)N, &s, &c);
+      else sincospi(-2.0 * (double)k / (double)N, &s, &c);
+      tw[k] = C{c, s};
+    }
+  }
+  for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
+    const int l = it % nlc, e = it / nlc;
+    a[e * nlc + l] = in[base + (size_t)((e + load_shift) % N) * N + l];
+  }
+  __syncthreads();
+  C *res = fft_exec(a, b, N, nlc, pl, sign, tw);
+  for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
+    const int l = it % nlc, e = it / nlc;
+    out[base + (size_t)((e + store_shift) % N) * N + l] = cscale(res[e * nlc + l], scale);
+  }
+}
+
+// ----------------------------------------------------------------- S1 ------
+// One CTA per (box row, chunk of nl channels): scatter beta' fhat into the
+// zero-padded row and FFT it along g2 with exp(+2 pi i).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_scatter_rowfft(const Cx<T> *__restrict__ fhat, const WedgeDev *__restrict__ W,
+                 const RowDev *__restrict__ rows, const FftPlanDev *__restrict__ ffts,
+                 const Cx<T> *__restrict__ tw_all, const Cx<T> *__restrict__ beta,
+                 Cx<T> *__restrict__ grid, int N, int B, int nl) {
+  using C = Cx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const RowDev rw = rows[blockIdx.x];
+  const WedgeDev w = W[rw.wedge];
+  const int nch = B * w.q;
+  const int c0 = blockIdx.y * nl;
+  if (c0 >= nch) return;
+  const int nlc = min(nl, nch - c0);
+  const int n = w.m2;
+  C *a = reinterpret_cast<C *>(smem_raw);
+  C *b = a + n * nl;
+  C *tw = b + n * nl;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw2_off + k];
+  for (int k = threadIdx.x; k < n * nlc; k += blockDim.x) a[k] = C{0, 0};
+  __syncthreads();
+  const int k1pp = rw.xi1 + w.xc1;
+  for (int it = threadIdx.x; it < rw.len * nlc; it += blockDim.x) {
+    const int l = it % nlc, j = it / nlc;
+    const int ch = c0 + l, bb = ch / w.q, t = ch - bb * w.q;
+    const int x2p = rw.a + j;
+    const int k2pp = x2p + w.xc2;
+    const int k1 = w.Minv[0] * k1pp + w.Minv[1] * k2pp;
+    const int k2 = w.Minv[2] * k1pp + w.Minv[3] * k2pp;
+    const size_t idx = (size_t)imodp(k1, N) * N + imodp(k2, N);
+    const C v = cmul(beta[w.beta_off + (long long)t * w.npts + rw.pt + j],
+                     fhat[(size_t)bb * N * N + idx]);
+    a[imodp(x2p, n) * nlc + l] = v;
+  }
+  __syncthreads();
+  const C *res = fft_exec(a, b, n, nlc, ffts[w.fft2], +1, tw);
+  C *out = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * n * nch + c0;
+  for (int it = threadIdx.x; it < n * nlc; it += blockDim.x) {
+    const int l = it % nlc, e = it / nlc;
+    out[(long long)e * nch + l] = res[e * nlc + l];
+  }
+}
+
+// ------------------------------------------------------------ S2 / S4b -----
+// Column FFTs along g1.  A CTA owns nl consecutive entries of the flattened
+// [g2][ch] dimension of one wedge.  adjoint = 0: input rows outside the box
+// are zero (not read), all m1 outputs written, exp(+2 pi i).  adjoint = 1:
+// all rows read, only box rows written, exp(-2 pi i).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
+         const FftPlanDev *__restrict__ ffts, const Cx<T> *__restrict__ tw_all, int L, int B,
+         int nl, int adjoint) {
+  using C = Cx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  // locate (wedge, chunk) for this block
+  int blk = blockIdx.x, l = 0;
+  for (; l < L; ++l) {
+    const int cnt = (W[l].m2 * B * W[l].q + nl - 1) / nl;
+    if (blk < cnt) break;
+    blk -= cnt;
+  }
+  if (l >= L) return;
+  const WedgeDev w = W[l];
+  const int nch = B * w.q;
+  const long long rs = (long long)w.m2 * nch;  // row stride
+  const long long cc0 = (long long)blk * nl;
+  const int nlc = (int)min((long long)nl, rs - cc0);
+  const int n = w.m1;
+  C *a = reinterpret_cast<C *>(smem_raw);
+  C *b = a + n * nl;
+  C *tw = b + n * nl;
+  C *g = grid + w.grid_unit * B + cc0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw1_off + k];
+  if (!adjoint) {
+    for (int k = threadIdx.x; k < n * nlc; k += blockDim.x) a[k] = C{0, 0};
+    __syncthreads();
+    for (int it = threadIdx.x; it < w.n1 * nlc; it += blockDim.x) {
+      const int c = it % nlc, e = it / nlc;
+      const int g1 = imodp(w.b1 + e, n);
+      a[g1 * nlc + c] = g[g1 * rs + c];
+    }
+  } else {
+    for (int it = threadIdx.x; it < n * nlc; it += blockDim.x) {
+      const int c = it % nlc, e = it / nlc;
+      a[e * nlc + c] = g[e * rs + c];
+    }
+  }
+  __syncthreads();
+  const C *res = fft_exec(a, b, n, nlc, ffts[w.fft1], adjoint ? -1 : +1, tw);
+  if (!adjoint) {
+    for (int it = threadIdx.x; it < n * nlc; it += blockDim.x) {
+      const int c = it % nlc, e = it / nlc;
+      g[e * rs + c] = res[e * nlc + c];
+    }
+  } else {
+    for (int it = threadIdx.x; it < w.n1 * nlc; it += blockDim.x) {
+      const int c = it % nlc, e = it / nlc;
+      const int g1 = imodp(w.b1 + e, n);
+      g[g1 * rs + c] = res[g1 * nlc + c];
+    }
+  }
+}
+
+// ----------------------------------------------------------------- S3 ------
+// One thread per (x, b): sum over wedges l and terms t of
+// alpha'_t(x) * sum_{cells} phi phi G_{l t}.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_interp(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
+         const Cx<T> *__restrict__ alpha, const uint2 *__restrict__ warp, Cx<T> *__restrict__ out,
+         int N, int L, int B, KbDev kb) {
+  using C = Cx<T>;
+  const long long NN = (long long)N * N;
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bb = blockIdx.y;
+  if (x >= NN) return;
+  T w1[kMaxKbWidth], w2[kMaxKbWidth];
+  C acc{0, 0};
+  for (int l = 0; l < L; ++l) {
+    const WedgeDev &w = W[l];
+    const uint2 Y = warp[l * NN + x];
+    const int j1 = kb_window<T>(Y.x, w.m1, kb, w1);
+    const int j2 = kb_window<T>(Y.y, w.m2, kb, w2);
+    const int nch = B * w.q;
+    const C *g = grid + w.grid_unit * B + bb * w.q;
+    for (int t = 0; t < w.q; ++t) {
+      C v{0, 0};
+      int c1 = j1;
+      for (int a1 = 0; a1 < kb.w; ++a1) {
+        C r{0, 0};
+        int c2 = j2;
+        const C *grow = g + (long long)c1 * w.m2 * nch + t;
+        for (int a2 = 0; a2 < kb.w; ++a2) {
+          const C gv = grow[(long long)c2 * nch];
+          r.x += w2[a2] * gv.x;
+          r.y += w2[a2] * gv.y;
+          if (++c2 == w.m2) c2 = 0;
+        }
+        v.x += w1[a1] * r.x;
+        v.y += w1[a1] * r.y;
+        if (++c1 == w.m1) c1 = 0;
+      }
+      const C al = alpha[w.alpha_off + t * NN + x];
+      acc = cadd(acc, cmul(al, v));
+    }
+  }
+  out[bb * NN + x] = acc;
+}
+
+// ----------------------------------------------------------------- S4a -----
+// Type-1 spread: G_{l t} += phi phi conj(alpha'_t(x)) g(x).
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_spread(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
+         const Cx<T> *__restrict__ alpha, const uint2 *__restrict__ warp, int N, int L, int B,
+         KbDev kb) {
+  using C = Cx<T>;
+  const long long NN = (long long)N * N;
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bb = blockIdx.y;
+  if (x >= NN) return;
+  T w1[kMaxKbWidth], w2[kMaxKbWidth];
+  const C gv = gin[bb * NN + x];
+  for (int l = 0; l < L; ++l) {
+    const WedgeDev &w = W[l];
+    const uint2 Y = warp[l * NN + x];
+    const int j1 = kb_window<T>(Y.x, w.m1, kb, w1);
+    const int j2 = kb_window<T>(Y.y, w.m2, kb, w2);
+    const int nch = B * w.q;
+    C *g = grid + w.grid_unit * B + bb * w.q;
+    for (int t = 0; t < w.q; ++t) {
+      const C c = cmulc(gv, alpha[w.alpha_off + t * NN + x]);  // g * conj(alpha)
+      int c1 = j1;
+      for (int a1 = 0; a1 < kb.w; ++a1) {
+        int c2 = j2;
+        T* grow = reinterpret_cast<T *>(g + (long long)c1 * w.m2 * nch + t);
+        for (int a2 = 0; a2 < kb.w; ++a2) {
+          const T wt = w1[a1] * w2[a2];
+          atomicAdd(grow + 2 * (long long)c2 * nch, wt * c.x);
+          atomicAdd(grow + 2 * (long long)c2 * nch + 1, wt * c.y);
+          if (++c2 == w.m2) c2 = 0;
+        }
+        if (++c1 == w.m1) c1 = 0;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- S4b rows --
+// Row FFT along g2 with exp(-2 pi i) for each box row; only the run's
+// columns are written back.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_rowfft_adj(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
+             const RowDev *__restrict__ rows, const FftPlanDev *__restrict__ ffts,
+             const Cx<T> *__restrict__ tw_all, int B, int nl) {
+  using C = Cx<T>;
+  extern __shared__ unsigned char smem_raw[];
+  const RowDev rw = rows[blockIdx.x];
+  const WedgeDev w = W[rw.wedge];
+  const int nch = B * w.q;
+  const int c0 = blockIdx.y * nl;
+  if (c0 >= nch || rw.len == 0) return;
+  const int nlc = min(nl, nch - c0);
+  const int n = w.m2;
+  C *a = reinterpret_cast<C *>(smem_raw);
+  C *b = a + n * nl;
+  C *tw = b + n * nl;
+  C *row = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * n * nch + c0;
+  for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw2_off + k];
+  for (int it = threadIdx.x; it < n * nlc; it += blockDim.x) {
+    const int l = it % nlc, e = it / nlc;
+    a[e * nlc + l] = row[(long long)e * nch + l];
+  }
+  __syncthreads();
+  const C *res = fft_exec(a, b, n, nlc, ffts[w.fft2], -1, tw);
+  for (int it = threadIdx.x; it < rw.len * nlc; it += blockDim.x) {
+    const int l = it % nlc, j = it / nlc;
+    const int g2 = imodp(rw.a + j, n);
+    row[(long long)g2 * nch + l] = res[g2 * nlc + l];
+  }
+}
+
+// ---------------------------------------------------------------- S4c ------
+// fhat_adj(xi) = sum_t conj(beta'_t(xi)) Ghat_{l t}(xi') for the owner wedge.
+template <typename T>
+__global__ void __launch_bounds__(kThreads)
+k_gather_adj(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
+             const RowDev *__restrict__ rows, const Cx<T> *__restrict__ beta,
+             Cx<T> *__restrict__ fhat, int N, int B) {
+  using C = Cx<T>;
+  const RowDev rw = rows[blockIdx.x];
+  const WedgeDev w = W[rw.wedge];
+  const int nch = B * w.q;
+  const C *row = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * w.m2 * nch;
+  const int k1pp = rw.xi1 + w.xc1;
+  for (int it = threadIdx.x; it < rw.len * B; it += blockDim.x) {
+    const int j = it % rw.len, bb = it / rw.len;
+    const int x2p = rw.a + j;
+    const C *cell = row + (long long)imodp(x2p, w.m2) * nch + bb * w.q;
+    C acc{0, 0};
+    for (int t = 0; t < w.q; ++t)
+      acc = cadd(acc, cmulc(cell[t], beta[w.beta_off + (long long)t * w.npts + rw.pt + j]));
+    const int k2pp = x2p + w.xc2;
+    const int k1 = w.Minv[0] * k1pp + w.Minv[1] * k2pp;
+    const int k2 = w.Minv[2] * k1pp + w.Minv[3] * k2pp;
+    fhat[(size_t)bb * N * N + (size_t)imodp(k1, N) * N + imodp(k2, N)] = acc;
+  }
+}
+
+// ============================================================= launchers ===
+
+size_t apply_smem_bytes(int n, int nl, int precision) {
+  const size_t cs = precision == FIO_FP64 ? 16 : 8;
+  return (2 * (size_t)n * nl + n) * cs;
+}
+
+static int pick_nl(int n, int precision, int want) {
+  const size_t budget = 96 * 1024;
+  int nl = want;
+  while (nl > 1 && apply_smem_bytes(n, nl, precision) > budget) nl >>= 1;
+  return nl;
+}
+
+template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
+  if (bytes <= 48 * 1024) return cudaSuccess;
+  return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+template <typename T>
+static cudaError_t dft2_impl(int N, const void *in, void *out, int batch, int inverse,
+                             const FftPlanDev &pl, const void *d_tw, bool centred,
+                             cudaStream_t s) {
+  using C = Cx<T>;
+  const int prec = sizeof(T) == 8 ? FIO_FP64 : FIO_MIXED;
+  const int nl = pick_nl(N, prec, 16);
+  const size_t smem = apply_smem_bytes(N, nl, prec);
+  cudaError_t e;
+  if ((e = set_smem(k_dft_rows<T>, smem)) != cudaSuccess) return e;
+  if ((e = set_smem(k_dft_cols<T>, smem)) != cudaSuccess) return e;
+  const int sign = inverse ? +1 : -1;
+  const int sh = centred ? N / 2 : 0;
+  const int nrows = batch * N;
+  // rows: forward stores shifted, inverse loads shifted
+  k_dft_rows<T><<<(nrows + nl - 1) / nl, kThreads, smem, s>>>(
+      (const C *)in, (C *)out, N, nrows, nl, sign, inverse ? sh : 0, inverse ? 0 : sh, pl,
+      (const C *)d_tw);
+  const int chunks = (N + nl - 1) / nl;
+  k_dft_cols<T><<<batch * chunks, kThreads, smem, s>>>((const C *)out, (C *)out, N, nl, sign,
+                                                      inverse ? sh : 0, inverse ? 0 : sh,
+                                                      T(1.0) / T(N), pl, (const C *)d_tw);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int batch, int inverse,
+                        const FftPlanDev *plan, const void *d_tw, cudaStream_t s) {
+  if (precision == FIO_FP64) return dft2_impl<double>(N, in, out, batch, inverse, *plan, d_tw, true, s);
+  return dft2_impl<float>(N, in, out, batch, inverse, *plan, d_tw, true, s);
+}
+
+static KbDev make_kb(const fio_plan_s *p) {
+  KbDev kb;
+  kb.w = p->kb.w;
+  kb.beta = p->kb.beta;
+  kb.inv_i0b = 1.0 / std::cyl_bessel_i(0.0, p->kb.beta);
+  return kb;
+}
+
+struct LaunchGeom {
+  int max_m1 = 0, max_m2 = 0, max_q = 0, col_blocks = 0;
+};
+
+static LaunchGeom geom(const fio_plan_s *p, int B, int nl_col) {
+  LaunchGeom g;
+  for (const auto &w : p->wedges) {
+    g.max_m1 = std::max(g.max_m1, w.m1);
+    g.max_m2 = std::max(g.max_m2, w.m2);
+    g.max_q = std::max(g.max_q, w.q);
+    g.col_blocks += (w.m2 * B * w.q + nl_col - 1) / nl_col;
+  }
+  return g;
+}
+
+static FftPlanDev plan_for_N(const fio_plan_s *p, const void **tw) {
+  for (const auto &f : p->ffts)
+    if (f.n == p->N) {
+      *tw = (const char *)p->d_twiddle + (size_t)f.tw_off * (p->precision == FIO_FP64 ? 16 : 8);
+      return f;
+    }
+  *tw = nullptr;
+  return FftPlanDev{};
+}
+
+template <typename T>
+static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int B,
+                              cudaStream_t s) {
+  using C = Cx<T>;
+  const int prec = p->precision;
+  const int N = p->N, L = p->L;
+  const long long NN = (long long)N * N;
+  const void *twN;
+  const FftPlanDev plN = plan_for_N(p, &twN);
+  cudaError_t e;
+  // S0: fhat in natural order (no centring shift)
+  e = dft2_impl<T>(N, f, p->d_fhat, B, 0, plN, twN, false, s);
+  if (e != cudaSuccess) return e;
+  const LaunchGeom g0 = geom(p, B, 1);
+  // S1
+  const int nl1 = pick_nl(g0.max_m2, prec, 16);
+  const size_t sm1 = apply_smem_bytes(g0.max_m2, nl1, prec);
+  if ((e = set_smem(k_scatter_rowfft<T>, sm1)) != cudaSuccess) return e;
+  dim3 g1((unsigned)p->rows.size(), (unsigned)((B * g0.max_q + nl1 - 1) / nl1));
+  k_scatter_rowfft<T><<<g1, kThreads, sm1, s>>>((const C *)p->d_fhat, p->d_wedges, p->d_rows,
+                                                p->d_ffts, (const C *)p->d_twiddle,
+                                                (const C *)p->d_beta, (C *)p->d_grid, N, B, nl1);
+  // S2
+  const int nl2 = pick_nl(g0.max_m1, prec, 16);
+  const size_t sm2 = apply_smem_bytes(g0.max_m1, nl2, prec);
+  if ((e = set_smem(k_colfft<T>, sm2)) != cudaSuccess) return e;
+  const LaunchGeom g2 = geom(p, B, nl2);
+  k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)p->d_grid, p->d_wedges, p->d_ffts,
+                                                   (const C *)p->d_twiddle, L, B, nl2, 0);
+  // S3
+  dim3 g3((unsigned)((NN + kThreads - 1) / kThreads), (unsigned)B);
+  k_interp<T><<<g3, kThreads, 0, s>>>((const C *)p->d_grid, p->d_wedges, (const C *)p->d_alpha,
+                                      p->d_warp, (C *)out, N, L, B, make_kb(p));
+  return cudaGetLastError();
+}
+
+template <typename T>
+static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out, int B,
+                                cudaStream_t s) {
+  using C = Cx<T>;
+  const int prec = p->precision;
+  const int N = p->N, L = p->L;
+  const long long NN = (long long)N * N;
+  cudaError_t e;
+  const size_t cs = prec == FIO_FP64 ? 16 : 8;
+  // S4a
+  e = cudaMemsetAsync(p->d_grid, 0, (size_t)p->grid_units * B * cs, s);
+  if (e != cudaSuccess) return e;
+  dim3 ga((unsigned)((NN + kThreads - 1) / kThreads), (unsigned)B);
+  k_spread<T><<<ga, kThreads, 0, s>>>((const C *)gin, (C *)p->d_grid, p->d_wedges,
+                                      (const C *)p->d_alpha, p->d_warp, N, L, B, make_kb(p));
+  // S4b columns
+  const LaunchGeom g0 = geom(p, B, 1);
+  const int nl2 = pick_nl(g0.max_m1, prec, 16);
+  const size_t sm2 = apply_smem_bytes(g0.max_m1, nl2, prec);
+  if ((e = set_smem(k_colfft<T>, sm2)) != cudaSuccess) return e;
+  const LaunchGeom g2 = geom(p, B, nl2);
+  k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)p->d_grid, p->d_wedges, p->d_ffts,
+                                                   (const C *)p->d_twiddle, L, B, nl2, 1);
+  // S4b rows
+  const int nl1 = pick_nl(g0.max_m2, prec, 16);
+  const size_t sm1 = apply_smem_bytes(g0.max_m2, nl1, prec);
+  if ((e = set_smem(k_rowfft_adj<T>, sm1)) != cudaSuccess) return e;
+  dim3 g1((unsigned)p->rows.size(), (unsigned)((B * g0.max_q + nl1 - 1) / nl1));
+  k_rowfft_adj<T><<<g1, kThreads, sm1, s>>>((C *)p->d_grid, p->d_wedges, p->d_rows, p->d_ffts,
+                                            (const C *)p->d_twiddle, B, nl1);
+  // S4c
+  k_gather_adj<T><<<(unsigned)p->rows.size(), kThreads, 0, s>>>(
+      (const C *)p->d_grid, p->d_wedges, p->d_rows, (const C *)p->d_beta, (C *)p->d_fhat, N, B);
+  // S4d: inverse unitary DFT from natural order
+  const void *twN;
+  const FftPlanDev plN = plan_for_N(p, &twN);
+  return dft2_impl<T>(N, p->d_fhat, out, B, 1, plN, twN, false, s);
+}
+
+cudaError_t launch_apply(const fio_plan_s *p, const void *f, void *out, int batch,
+                         cudaStream_t s) {
+  if (p->precision == FIO_FP64) return apply_impl<double>(p, f, out, batch, s);
+  return apply_impl<float>(p, f, out, batch, s);
+}
+
+cudaError_t launch_adjoint(const fio_plan_s *p, const void *g, void *out, int batch,
+                           cudaStream_t s) {
+  if (p->precision == FIO_FP64) return adjoint_impl<double>(p, g, out, batch, s);
+  return adjoint_impl<float>(p, g, out, batch, s);
+}
+
+}  // namespace fio

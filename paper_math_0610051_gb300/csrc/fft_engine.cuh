@@ -1,0 +1,170 @@
+// fft_engine.cuh -- batched 1D FFTs in shared memory (Stockham autosort,
+// mixed radix 2/3/4/5/8), used by every grid stage of the apply path.
+//
+// Data of `nl` lines of length n sit in shared memory element-major: element e
+// of line l is at buf[e * nl + l].  This is the natural layout of the NUFFT
+// grids, whose innermost dimension is the channel (batch, rank term), so the
+// lines of a CTA are contiguous in global memory.
+//
+// Transform convention: X[k] = sum_j x[j] exp(sign * 2 pi i j k / n), sign = +-1,
+// unnormalised.  Twiddles come from a table tw[k] = exp(-2 pi i k / n) (k < n)
+// that the caller places in shared memory.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "fio_internal.h"
+
+namespace fio {
+
+template <typename T> struct CxT;
+template <> struct CxT<float> { using type = float2; };
+template <> struct CxT<double> { using type = double2; };
+
+template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return {a.x + b.x, a.y + b.y}; }
+template <typename C> __device__ __forceinline__ C csub(C a, C b) { return {a.x - b.x, a.y - b.y}; }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x};
+}
+template <typename C> __device__ __forceinline__ C cmulc(C a, C b) {  // a * conj(b)
+  return {a.x * b.x + a.y * b.y, a.y * b.x - a.x * b.y};
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { return {a.x, -a.y}; }
+template <typename C, typename T> __device__ __forceinline__ C cscale(C a, T s) {
+  return {a.x * s, a.y * s};
+}
+// i * sign * a
+template <typename C> __device__ __forceinline__ C cmul_si(C a, int sign) {
+  return sign > 0 ? C{-a.y, a.x} : C{a.y, -a.x};
+}
+
+// ---------------------------------------------------------------- butterflies
+// V[k] = sum_r v[r] exp(sign 2 pi i r k / R)
+
+template <typename C> __device__ __forceinline__ void bfly2(C *v) {
+  C a = v[0], b = v[1];
+  v[0] = cadd(a, b);
+  v[1] = csub(a, b);
+}
+
+template <typename C> __device__ __forceinline__ void bfly4(C *v, int sign) {
+  C s02 = cadd(v[0], v[2]), d02 = csub(v[0], v[2]);
+  C s13 = cadd(v[1], v[3]), d13 = cmul_si(csub(v[1], v[3]), sign);
+  v[0] = cadd(s02, s13);
+  v[2] = csub(s02, s13);
+  v[1] = cadd(d02, d13);
+  v[3] = csub(d02, d13);
+}
+
+template <typename C> __device__ __forceinline__ void bfly3(C *v, int sign) {
+  using T = decltype(v[0].x);
+  const T c1 = T(-0.5);
+  const T s1 = T(0.86602540378443864676372317075294);  // sin(2 pi / 3)
+  C t1 = cadd(v[1], v[2]);
+  C m = cadd(v[0], cscale(t1, c1));
+  C d = cmul_si(cscale(csub(v[1], v[2]), s1), sign);
+  v[0] = cadd(v[0], t1);
+  v[1] = cadd(m, d);
+  v[2] = csub(m, d);
+}
+
+template <typename C> __device__ __forceinline__ void bfly5(C *v, int sign) {
+  using T = decltype(v[0].x);
+  const T c1 = T(0.30901699437494742410229341718282);   // cos(2 pi / 5)
+  const T c2 = T(-0.80901699437494742410229341718282);  // cos(4 pi / 5)
+  const T s1 = T(0.95105651629515357211643933337938);   // sin(2 pi / 5)
+  const T s2 = T(0.58778525229247312916870595463907);   // sin(4 pi / 5)
+  C a14 = cadd(v[1], v[4]), d14 = csub(v[1], v[4]);
+  C a23 = cadd(v[2], v[3]), d23 = csub(v[2], v[3]);
+  C m1 = cadd(v[0], cadd(cscale(a14, c1), cscale(a23, c2)));
+  C m2 = cadd(v[0], cadd(cscale(a14, c2), cscale(a23, c1)));
+  C n1 = cmul_si(cadd(cscale(d14, s1), cscale(d23, s2)), sign);
+  C n2 = cmul_si(csub(cscale(d14, s2), cscale(d23, s1)), sign);
+  v[0] = cadd(v[0], cadd(a14, a23));
+  v[1] = cadd(m1, n1);
+  v[4] = csub(m1, n1);
+  v[2] = cadd(m2, n2);
+  v[3] = csub(m2, n2);
+}
+
+template <typename C> __device__ __forceinline__ void bfly8(C *v, int sign) {
+  using T = decltype(v[0].x);
+  const T r2 = T(0.70710678118654752440084436210485);
+  C e[4] = {v[0], v[2], v[4], v[6]};
+  C o[4] = {v[1], v[3], v[5], v[7]};
+  bfly4(e, sign);
+  bfly4(o, sign);
+  // o[k] *= exp(sign 2 pi i k / 8)
+  C w1 = {r2, T(sign) * r2}, w3 = {-r2, T(sign) * r2};
+  o[1] = cmul(o[1], w1);
+  o[2] = cmul_si(o[2], sign);
+  o[3] = cmul(o[3], w3);
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    v[k] = cadd(e[k], o[k]);
+    v[k + 4] = csub(e[k], o[k]);
+  }
+}
+
+template <int R, typename C> __device__ __forceinline__ void bfly(C *v, int sign) {
+  if constexpr (R == 2) bfly2(v);
+  if constexpr (R == 3) bfly3(v, sign);
+  if constexpr (R == 4) bfly4(v, sign);
+  if constexpr (R == 5) bfly5(v, sign);
+  if constexpr (R == 8) bfly8(v, sign);
+}
+
+// One Stockham stage (decimation in time): for butterfly j of each line,
+// read v[r] = in[j + r n/R], twiddle by w^(k r) with k = j mod Ns and
+// w = exp(sign 2 pi i / (Ns R)), DFT_R, write to out[(j/Ns) Ns R + k + r Ns].
+template <int R, typename C>
+__device__ __forceinline__ void fft_stage(const C *__restrict__ in, C *__restrict__ out, int n,
+                                          int nl, int Ns, int sign, const C *__restrict__ tw) {
+  const int nb = n / R;
+  const int step = n / (Ns * R);
+  for (int it = threadIdx.x; it < nb * nl; it += blockDim.x) {
+    const int l = it % nl, j = it / nl;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = in[(j + r * nb) * nl + l];
+    const int k = j % Ns;
+    if (Ns > 1) {
+#pragma unroll
+      for (int r = 1; r < R; ++r) {
+        C t = tw[k * r * step];
+        if (sign > 0) t.y = -t.y;
+        v[r] = cmul(v[r], t);
+      }
+    }
+    bfly<R>(v, sign);
+    const int d = (j / Ns) * Ns * R + k;
+#pragma unroll
+    for (int r = 0; r < R; ++r) out[(d + r * Ns) * nl + l] = v[r];
+  }
+}
+
+// Run all stages of plan `pl` on buffer a (scratch b).  Returns the buffer
+// holding the result.  Must be called by all threads of the block; ends with
+// __syncthreads().  The caller synchronises before the call.
+template <typename C>
+__device__ C *fft_exec(C *a, C *b, int n, int nl, const FftPlanDev &pl, int sign, const C *tw) {
+  int Ns = 1;
+  for (int s = 0; s < pl.nstages; ++s) {
+    const int R = pl.radix[s];
+    switch (R) {
+      case 8: fft_stage<8>(a, b, n, nl, Ns, sign, tw); break;
+      case 4: fft_stage<4>(a, b, n, nl, Ns, sign, tw); break;
+      case 2: fft_stage<2>(a, b, n, nl, Ns, sign, tw); break;
+      case 3: fft_stage<3>(a, b, n, nl, Ns, sign, tw); break;
+      case 5: fft_stage<5>(a, b, n, nl, Ns, sign, tw); break;
+    }
+    __syncthreads();
+    C *t = a;
+    a = b;
+    b = t;
+    Ns *= R;
+  }
+  return a;
+}
+
+}  // namespace fio

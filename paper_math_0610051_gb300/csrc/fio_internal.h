@@ -1,0 +1,154 @@
+// fio_internal.h -- plan layout shared by the host code and the CUDA kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/fio.h"
+
+namespace fio {
+
+constexpr int kMaxRadixStages = 16;
+constexpr int kMaxFftLen = 4096;
+constexpr int kMaxKbWidth = 16;
+
+// One FFT length: its radix factorisation (Stockham stages) and where its
+// twiddle table exp(-2 pi i k / n), k < n, starts in the plan's table.
+struct FftPlanDev {
+  int n;
+  int nstages;
+  int radix[kMaxRadixStages];
+  int tw_off;  // complex offset into the twiddle table
+};
+
+// One wedge W_l after the shear/translation of Sec. 3.4: xi' = M xi - xi_c.
+struct WedgeDev {
+  int M[4];       // xi'' = M xi (row-major), det M = 1
+  int Minv[4];    // xi = Minv xi''
+  int xc1, xc2;   // translation xi_c
+  int b1, n1;     // rows    xi'_1 in [b1, b1 + n1)
+  int b2, n2;     // columns xi'_2 in [b2, b2 + n2)
+  int m1, m2;     // oversampled grid dims
+  int q;          // separation rank
+  int npts;       // |W_l|
+  int fft1, fft2;         // FftPlanDev index for lengths m1, m2
+  int row_off;            // first RowDev of this wedge
+  long long grid_unit;    // grid offset in units of complex * batch: sum_{l'<l} m1 m2 q
+  long long alpha_off;    // complex offset of alpha[l][0][0] (layout [t][x])
+  long long beta_off;     // complex offset of beta[l][0][0]  (layout [t][p])
+  int pt_off;             // first point of this wedge in the global point order
+  int tw1_off, tw2_off;   // twiddle offsets for m1 / m2 (copies of the FftPlanDev fields)
+};
+
+// One box row xi'_1 = b1 + r: the wedge's frequencies on it are the contiguous
+// run xi'_2 in [a, a + len) (a convex cone meets a lattice line in a run).
+struct RowDev {
+  int wedge;
+  int xi1;     // xi'_1
+  int a, len;  // run of xi'_2
+  int pt;      // index of the run's first point within the wedge's point list
+};
+
+// KB kernel phi(s) = I0(beta sqrt(1 - (2s/w)^2)), |s| <= w/2.
+struct KbParams {
+  int w;
+  double beta;
+};
+
+struct PlanHost;  // host-side mirror, defined in plan.cpp
+
+}  // namespace fio
+
+// The plan object behind the opaque fio_plan handle.
+struct fio_plan_s {
+  int N = 0, L = 0, precision = FIO_MIXED, max_batch = 1;
+  double eps = 0, sigma = 2.0, plan_seconds = 0;
+  fio::KbParams kb{};
+  int q_max = 0, q_min = 0, r_max = 0;
+  double q_mean = 0;
+  int device = 0;
+
+  // host copies of the tables
+  std::vector<fio::WedgeDev> wedges;
+  std::vector<fio::RowDev> rows;
+  std::vector<fio::FftPlanDev> ffts;
+  std::vector<int> wedge_r;
+  std::vector<int> pt_k1, pt_k2;   // every frequency, wedge by wedge, row-major in each box
+  long long grid_units = 0;        // sum_l m1 m2 q
+  long long alpha_elems = 0, beta_elems = 0;
+  int max_row_len = 0;
+
+  // device arrays
+  fio::WedgeDev *d_wedges = nullptr;
+  fio::RowDev *d_rows = nullptr;
+  fio::FftPlanDev *d_ffts = nullptr;
+  void *d_twiddle = nullptr;      // complex (float2 / double2) exp(-2 pi i k/n) tables
+  void *d_alpha = nullptr;        // gamma^x * centre phase / N, [l][t][x]
+  void *d_beta = nullptr;         // gamma^xi / phihat, [l][t][p]
+  uint2 *d_warp = nullptr;        // warped points y' mod 1 as 32-bit fractions, [l][x]
+  void *d_grid = nullptr;         // NUFFT grids [l][g1][g2][b*q + t]
+  void *d_fhat = nullptr;         // spectrum workspace, batch * N * N complex
+  size_t bytes_total = 0;
+  unsigned long long alg_bytes = 0;
+
+};
+
+namespace fio {
+
+// Thread-local error text (api.cpp).
+void set_error(const std::string &msg);
+
+// plan.cpp
+fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_amplitude *amp,
+                      double eps, const fio_options *opt);
+void free_plan_device(fio_plan_s *p);
+
+// Host helpers shared by plan.cpp and the launchers.
+std::vector<int> fft_factor(int n);   // radices (8, 4, 2, 3, 5), empty if n is not 2^a 3^b 5^c
+int fft_good_size(int n);             // smallest even 2^a 3^b 5^c >= n
+
+// apply.cu launchers (return cudaGetLastError()).
+cudaError_t launch_apply(const fio_plan_s *p, const void *f, void *out, int batch,
+                         cudaStream_t s);
+cudaError_t launch_adjoint(const fio_plan_s *p, const void *g, void *out, int batch,
+                           cudaStream_t s);
+cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int batch, int inverse,
+                        const FftPlanDev *d_plan, const void *d_tw, cudaStream_t s);
+size_t apply_smem_bytes(int n, int nl, int precision);
+
+// plan_kernels.cu (FP64 plan construction on the device)
+struct PhaseDev {
+  int kind;
+  int nmodes;
+  double p[8];       // scalar parameters (shift/wave, ellipse)
+  int amp_kind;
+  double a1, a2;
+};
+
+cudaError_t plan_xdata(const PhaseDev &ph, const double *d_modes, int N, void *d_xdata,
+                       cudaStream_t s);
+size_t plan_xdata_bytes(const PhaseDev &ph, int N);
+cudaError_t plan_warp(const PhaseDev &ph, const void *d_xdata, int N, int L, const WedgeDev *d_w,
+                      uint2 *d_warp, cudaStream_t s);
+// A_C[x][c] = a(x, xi_c) exp(2 pi i Phi_l(x, xi_c)) for the sampled columns of wedge l.
+cudaError_t plan_eval_cols(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
+                           const uint2 *d_warp_l, const int *d_ck1, const int *d_ck2, int r,
+                           double2 *d_AC, cudaStream_t s);
+// Gram matrix G = A_C^H A_C (r x r), deterministic two-level reduction.
+cudaError_t plan_gram(const double2 *d_AC, long long rows, int r, double2 *d_partial,
+                      int nparts, double2 *d_G, cudaStream_t s);
+// alpha[t][x] = (sum_c A_C[x][c] W[c][t]) * exp(2 pi i y'.xi_c) / N  (W = V S^-1, r x q)
+cudaError_t plan_form_alpha(const double2 *d_AC, int N, int r, int q, const double2 *d_W,
+                            const WedgeDev &w, const uint2 *d_warp_l, void *d_alpha_l,
+                            int precision, cudaStream_t s);
+// beta[t][p] = (sum_i P[t][i] A(x_i, xi_p)) * dec[p], P = U_R^+ (q x r),
+// dec[p] = 1 / (phihat(xi'_1/m1) phihat(xi'_2/m2)) (NUFFT deconvolution)
+cudaError_t plan_form_beta(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
+                           const uint2 *d_warp_l, const int *d_rx, int r, int q,
+                           const double2 *d_P, const int *d_pk1, const int *d_pk2,
+                           const double *d_dec, void *d_beta_l, int precision, cudaStream_t s);
+
+}  // namespace fio

@@ -1,0 +1,716 @@
+// plan.cpp -- host side of fio_plan_create: polar wedges (Sec. 1.3), the
+// shear/translate boxes and NUFFT grids (Sec. 3.4), the Kaiser-Bessel kernel,
+// and the randomized separation of Sec. 3.2 (sample columns, SVD through the
+// Gram matrix, threshold eps, double r until q <= r/3, sample rows,
+// T = U_[R]^+ A_[R]).  Large FP64 work runs in plan_kernels.cu; the r x r and
+// q x q eigenproblems run here.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <complex>
+#include <cstdlib>
+#include <cstring>
+#include <numeric>
+#include <set>
+#include <string>
+#include <unordered_set>
+#include <vector>
+
+#include "fio_internal.h"
+#include "plan_host.h"
+
+namespace fio {
+
+using cd = std::complex<double>;
+
+// ------------------------------------------------------------- FFT sizes --
+
+std::vector<int> fft_factor(int n) {
+  std::vector<int> r;
+  if (n < 2) return r;
+  while (n % 8 == 0) { r.push_back(8); n /= 8; }
+  while (n % 4 == 0) { r.push_back(4); n /= 4; }
+  while (n % 2 == 0) { r.push_back(2); n /= 2; }
+  while (n % 3 == 0) { r.push_back(3); n /= 3; }
+  while (n % 5 == 0) { r.push_back(5); n /= 5; }
+  if (n != 1) r.clear();
+  return r;
+}
+
+int fft_good_size(int n) {
+  for (int m = std::max(n, 2);; ++m)
+    if (m % 2 == 0 && !fft_factor(m).empty()) return m;
+}
+
+// ---------------------------------------------------------- KB kernel ------
+
+int kb_width_for(double eps) {
+  // 1D relative NUFFT error of the sigma = 2 KB kernel is about 4.5 * 10^-w
+  // (measured against direct sums); ask for eps / 10.
+  int w = (int)std::ceil(std::log10(45.0 / eps));
+  return std::min(std::max(w, 2), kMaxKbWidth);
+}
+
+double kb_beta_for(int w, double sigma) {
+  // Beatty, Nishimura, Pauly (2005): beta = pi sqrt((w/sigma)^2 (sigma - 1/2)^2 - 0.8)
+  const double a = (w / sigma) * (w / sigma) * (sigma - 0.5) * (sigma - 0.5) - 0.8;
+  return M_PI * std::sqrt(std::max(a, 0.1));
+}
+
+double kb_phi_host(double s, int w, double beta) {
+  const double z = 2.0 * s / w, a = 1.0 - z * z;
+  return a > 0 ? std::cyl_bessel_i(0.0, beta * std::sqrt(a)) / std::cyl_bessel_i(0.0, beta) : 0.0;
+}
+
+// phihat(nu) = int phi(s) exp(-2 pi i nu s) ds = w sinh(sqrt(b^2 - a^2)) / sqrt(b^2 - a^2) / I0(b),
+// a = pi w nu (the sin form when a > b).
+double kb_phihat_host(double nu, int w, double beta) {
+  const double a = M_PI * w * nu;
+  const double d = beta * beta - a * a;
+  double v;
+  if (d > 1e-12) v = w * std::sinh(std::sqrt(d)) / std::sqrt(d);
+  else if (d < -1e-12) v = w * std::sin(std::sqrt(-d)) / std::sqrt(-d);
+  else v = w;
+  return v / std::cyl_bessel_i(0.0, beta);
+}
+
+// -------------------------------------------------------------- wedges -----
+
+int default_L(int N) {
+  int L = (int)std::ceil(std::sqrt((double)N) - 1e-12);
+  L = (L + 7) / 8 * 8;
+  return std::max(L, 8);
+}
+
+// W_l = {(2l - 1) pi / L <= arg xi < (2l + 1) pi / L}; xi = 0 belongs to wedge 0.
+int wedge_of(int k1, int k2, int L) {
+  if (k1 == 0 && k2 == 0) return 0;
+  const double th = std::atan2((double)k2, (double)k1);
+  int l = (int)std::floor((th + M_PI / L) / (2.0 * M_PI / L));
+  l %= L;
+  if (l < 0) l += L;
+  return l;
+}
+
+static const int kShears[5][4] = {
+    {1, 0, 0, 1}, {1, 0, -1, 1}, {1, 0, 1, 1}, {1, -1, 0, 1}, {1, 1, 0, 1}};
+static const int kShearInv[5][4] = {
+    {1, 0, 0, 1}, {1, 0, 1, 1}, {1, 0, -1, 1}, {1, 1, 0, 1}, {1, -1, 0, 1}};
+
+static int grid_len(int n, double sigma, int w) {
+  const int want = std::max({(int)std::ceil(sigma * n - 1e-9), n + 2, 2 * w, 16});
+  return fft_good_size(want);
+}
+
+// Box, grid and row runs for one wedge, choosing among identity and the four
+// 45-degree shears the one with the smallest oversampled grid (Sec. 3.4).
+bool wedge_geometry(const std::vector<std::pair<int, int>> &pts, double sigma, int w,
+                    WedgeDev &wd, std::vector<RowDev> &rows, std::vector<int> &k1s,
+                    std::vector<int> &k2s, std::vector<int> &x1p, std::vector<int> &x2p,
+                    std::string &err) {
+  long long best = -1;
+  int bi = 0;
+  for (int s = 0; s < 5; ++s) {
+    const int *M = kShears[s];
+    int lo1 = 1 << 30, hi1 = -(1 << 30), lo2 = 1 << 30, hi2 = -(1 << 30);
+    for (auto &p : pts) {
+      const int a = M[0] * p.first + M[1] * p.second, b = M[2] * p.first + M[3] * p.second;
+      lo1 = std::min(lo1, a); hi1 = std::max(hi1, a);
+      lo2 = std::min(lo2, b); hi2 = std::max(hi2, b);
+    }
+    const long long cost = (long long)grid_len(hi1 - lo1 + 1, sigma, w) *
+                           grid_len(hi2 - lo2 + 1, sigma, w);
+    if (best < 0 || cost < best) { best = cost; bi = s; }
+  }
+  std::memset(&wd, 0, sizeof(wd));
+  std::memcpy(wd.M, kShears[bi], sizeof(wd.M));
+  std::memcpy(wd.Minv, kShearInv[bi], sizeof(wd.Minv));
+  const int *M = wd.M;
+  std::vector<std::pair<int, int>> pp;  // (xi''_1, xi''_2)
+  pp.reserve(pts.size());
+  int lo1 = 1 << 30, hi1 = -(1 << 30), lo2 = 1 << 30, hi2 = -(1 << 30);
+  for (auto &p : pts) {
+    const int a = M[0] * p.first + M[1] * p.second, b = M[2] * p.first + M[3] * p.second;
+    pp.push_back({a, b});
+    lo1 = std::min(lo1, a); hi1 = std::max(hi1, a);
+    lo2 = std::min(lo2, b); hi2 = std::max(hi2, b);
+  }
+  const int n1 = hi1 - lo1 + 1, n2 = hi2 - lo2 + 1;
+  wd.xc1 = lo1 + n1 / 2;
+  wd.xc2 = lo2 + n2 / 2;
+  wd.b1 = lo1 - wd.xc1;
+  wd.n1 = n1;
+  wd.b2 = lo2 - wd.xc2;
+  wd.n2 = n2;
+  wd.m1 = grid_len(n1, sigma, w);
+  wd.m2 = grid_len(n2, sigma, w);
+  wd.npts = (int)pts.size();
+  std::sort(pp.begin(), pp.end());
+  rows.clear();
+  k1s.clear(); k2s.clear(); x1p.clear(); x2p.clear();
+  size_t i = 0;
+  for (int a = lo1; a <= hi1; ++a) {
+    RowDev rw{};
+    rw.xi1 = a - wd.xc1;
+    rw.pt = (int)k1s.size();
+    rw.len = 0;
+    rw.a = 0;
+    int prev = 0;
+    while (i < pp.size() && pp[i].first == a) {
+      const int b = pp[i].second;
+      if (rw.len == 0) rw.a = b - wd.xc2;
+      else if (b != prev + 1) {
+        err = "wedge row is not a contiguous run";
+        return false;
+      }
+      prev = b;
+      const int kk1 = wd.Minv[0] * a + wd.Minv[1] * b, kk2 = wd.Minv[2] * a + wd.Minv[3] * b;
+      k1s.push_back(kk1);
+      k2s.push_back(kk2);
+      x1p.push_back(a - wd.xc1);
+      x2p.push_back(b - wd.xc2);
+      ++rw.len;
+      ++i;
+    }
+    rows.push_back(rw);
+  }
+  return true;
+}
+
+// -------------------------------------------------------------- sampling ---
+
+struct SplitMix64 {  // Steele, Lea and Flood (2014)
+  uint64_t s;
+  uint64_t next() {
+    uint64_t z = (s += 0x9E3779B97F4A7C15ULL);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return z ^ (z >> 31);
+  }
+  uint64_t below(uint64_t n) { return (uint64_t)(((unsigned __int128)next() * n) >> 64); }
+};
+
+// k distinct integers of [0, n), uniformly (Floyd's algorithm), sorted.
+static std::vector<int> sample_distinct(int n, int k, SplitMix64 &rng) {
+  std::unordered_set<int> S;
+  S.reserve(2 * k);
+  for (int j = n - k; j < n; ++j) {
+    const int t = (int)rng.below((uint64_t)j + 1);
+    if (!S.insert(t).second) S.insert(j);
+  }
+  std::vector<int> v(S.begin(), S.end());
+  std::sort(v.begin(), v.end());
+  return v;
+}
+
+static uint64_t mix_seed(uint64_t seed, uint64_t a, uint64_t b) {
+  SplitMix64 m{seed ^ (a * 0xD1B54A32D192ED03ULL) ^ (b * 0x8CB92BA72F3D8DD7ULL)};
+  return m.next();
+}
+
+// ---------------------------------------------------------- eigensolver ----
+
+// Cyclic Jacobi for a Hermitian n x n matrix A (row-major); eigenvalues in
+// descending order, eigenvectors as the columns of V (row-major).
+void herm_eig(int n, std::vector<cd> A, std::vector<double> &ev, std::vector<cd> &V) {
+  V.assign((size_t)n * n, cd(0));
+  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
+  auto at = [&](int i, int j) -> cd & { return A[(size_t)i * n + j]; };
+  double diag = 0;
+  for (int i = 0; i < n; ++i) diag += std::norm(at(i, i));
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0;
+    for (int i = 0; i < n; ++i)
+      for (int j = i + 1; j < n; ++j) off += std::norm(at(i, j));
+    if (off <= 1e-32 * std::max(diag, 1e-300)) break;
+    for (int p = 0; p < n; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        const cd b = at(p, q);
+        const double ab = std::abs(b);
+        if (ab == 0.0) continue;
+        const double app = at(p, p).real(), aqq = at(q, q).real();
+        if (ab < 1e-300 || (std::abs(app) + ab == std::abs(app) && std::abs(aqq) + ab == std::abs(aqq) &&
+                            sweep > 4)) {
+          at(p, q) = 0; at(q, p) = 0;
+          continue;
+        }
+        const cd e = b / ab;
+        const double tau = (aqq - app) / (2.0 * ab);
+        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
+        // U = [[c, s], [-s conj(e), c conj(e)]] on (p, q); A <- U^H A U, V <- V U
+        const cd upq = s, uqp = -s * std::conj(e), uqq = c * std::conj(e);
+        for (int k = 0; k < n; ++k) {  // columns
+          const cd akp = at(k, p), akq = at(k, q);
+          at(k, p) = akp * c + akq * uqp;
+          at(k, q) = akp * upq + akq * uqq;
+          const cd vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
+          V[(size_t)k * n + p] = vkp * c + vkq * uqp;
+          V[(size_t)k * n + q] = vkp * upq + vkq * uqq;
+        }
+        for (int k = 0; k < n; ++k) {  // rows
+          const cd apk = at(p, k), aqk = at(q, k);
+          at(p, k) = c * apk + std::conj(uqp) * aqk;
+          at(q, k) = std::conj(upq) * apk + std::conj(uqq) * aqk;
+        }
+        at(p, q) = 0;
+        at(q, p) = 0;
+        at(p, p) = at(p, p).real();
+        at(q, q) = at(q, q).real();
+      }
+  }
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return at(a, a).real() > at(b, b).real(); });
+  ev.resize(n);
+  std::vector<cd> Vs((size_t)n * n);
+  for (int j = 0; j < n; ++j) {
+    ev[j] = at(idx[j], idx[j]).real();
+    for (int i = 0; i < n; ++i) Vs[(size_t)i * n + j] = V[(size_t)i * n + idx[j]];
+  }
+  V.swap(Vs);
+}
+
+// ------------------------------------------------------ device bookkeeping --
+
+namespace {
+
+struct DevAllocs {
+  std::vector<void *> ptrs;
+  ~DevAllocs() {
+    for (void *p : ptrs) cudaFree(p);
+  }
+};
+
+int g_fault_countdown = -1;  // FIO_FAULT_ALLOC=k: the k-th device allocation fails
+
+cudaError_t dev_alloc(void **p, size_t bytes) {
+  if (g_fault_countdown > 0 && --g_fault_countdown == 0) {
+    *p = nullptr;
+    return cudaErrorMemoryAllocation;
+  }
+  return cudaMalloc(p, std::max<size_t>(bytes, 16));
+}
+
+fio_status cuda_status(cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return FIO_OK;
+  set_error(std::string(what) + ": " + cudaGetErrorString(e));
+  return e == cudaErrorMemoryAllocation ? FIO_ENOMEM : FIO_ECUDA;
+}
+
+}  // namespace
+
+#define FIO_CK(expr, what)                                  \
+  do {                                                      \
+    fio_status st_ = cuda_status((expr), (what));           \
+    if (st_ != FIO_OK) return st_;                          \
+  } while (0)
+
+void free_plan_device(fio_plan_s *p) {
+  void *ptrs[] = {p->d_wedges, p->d_rows,  p->d_ffts, p->d_twiddle, p->d_alpha,
+                  p->d_beta,   p->d_warp,  p->d_grid, p->d_fhat};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  p->d_wedges = nullptr; p->d_rows = nullptr; p->d_ffts = nullptr; p->d_twiddle = nullptr;
+  p->d_alpha = nullptr; p->d_beta = nullptr; p->d_warp = nullptr; p->d_grid = nullptr;
+  p->d_fhat = nullptr;
+}
+
+template <typename T> static fio_status upload(void **dst, const std::vector<T> &v, const char *w) {
+  FIO_CK(dev_alloc(dst, v.size() * sizeof(T)), w);
+  if (!v.empty()) FIO_CK(cudaMemcpy(*dst, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice), w);
+  return FIO_OK;
+}
+
+template <typename T>
+static fio_status upload_tmp(DevAllocs &tmp, T **dst, const std::vector<T> &v, const char *w) {
+  void *p = nullptr;
+  fio_status s = upload(&p, v, w);
+  if (p) tmp.ptrs.push_back(p);
+  *dst = (T *)p;
+  return s;
+}
+
+static bool finite_all(const double *p, int n) {
+  for (int i = 0; i < n; ++i)
+    if (!std::isfinite(p[i])) return false;
+  return true;
+}
+
+// ------------------------------------------------------------ build_plan --
+
+fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_amplitude *amp,
+                      double eps, const fio_options *opt_in) {
+  const auto t_start = std::chrono::steady_clock::now();
+  fio_options opt;
+  fio_options_default(&opt);
+  if (opt_in) opt = *opt_in;
+  const char *fa = std::getenv("FIO_FAULT_ALLOC");
+  g_fault_countdown = fa ? std::atoi(fa) : -1;
+
+  // ---- validation
+  if (N < 8 || N > 2048 || (N & 1)) { set_error("N must be even, 8 <= N <= 2048"); return FIO_EINVAL; }
+  if (!(eps >= 1e-12 && eps <= 0.1)) { set_error("eps must lie in [1e-12, 0.1]"); return FIO_EINVAL; }
+  if (!phase || phase->kind < 0 || phase->kind > 2 || !phase->params) {
+    set_error("invalid phase descriptor");
+    return FIO_EINVAL;
+  }
+  const int nscal = phase->kind == FIO_PHASE_SHIFT_WAVE ? 3 : phase->kind == FIO_PHASE_ELLIPSE ? 4 : 0;
+  if (phase->kind == FIO_PHASE_TAU_MODES) {
+    if (phase->nmodes < 1 || phase->nmodes > 65536) { set_error("nmodes out of range"); return FIO_EINVAL; }
+    if (!finite_all(phase->params, 5 * phase->nmodes)) { set_error("non-finite phase parameter"); return FIO_EINVAL; }
+    for (int j = 0; j < phase->nmodes; ++j) {
+      const double m = phase->params[5 * j + 3];
+      if (m != std::floor(m) || std::abs(m) > 8) { set_error("tau mode m must be an integer in [-8, 8]"); return FIO_EINVAL; }
+    }
+  } else if (!finite_all(phase->params, nscal)) {
+    set_error("non-finite phase parameter");
+    return FIO_EINVAL;
+  }
+  const fio_amplitude amp1 = amp ? *amp : fio_amplitude{FIO_AMP_ONE, 0, 0};
+  if (amp1.kind < 0 || amp1.kind > 1 || !std::isfinite(amp1.a1) || !std::isfinite(amp1.a2)) {
+    set_error("invalid amplitude");
+    return FIO_EINVAL;
+  }
+  if (opt.precision != FIO_MIXED && opt.precision != FIO_FP64) { set_error("invalid precision"); return FIO_EINVAL; }
+  const int L = opt.L > 0 ? opt.L : default_L(N);
+  const double sigma = opt.sigma > 0 ? opt.sigma : 2.0;
+  if (L < 1 || L > 256 || sigma < 1.25 || sigma > 4.0) { set_error("L or sigma out of range"); return FIO_EINVAL; }
+  const int w = opt.kb_width > 0 ? opt.kb_width : kb_width_for(eps);
+  if (w < 2 || w > kMaxKbWidth) { set_error("kb_width out of range"); return FIO_EINVAL; }
+  const int r0 = opt.r0 > 0 ? opt.r0 : 8;
+  const int rank_cap = opt.rank_cap > 0 ? opt.rank_cap : 512;
+  const int max_batch = opt.max_batch > 0 ? opt.max_batch : 1;
+  if (max_batch > 4096) { set_error("max_batch too large"); return FIO_EINVAL; }
+
+  p->N = N; p->L = L; p->eps = eps; p->sigma = sigma; p->precision = opt.precision;
+  p->max_batch = max_batch;
+  p->kb.w = w;
+  p->kb.beta = kb_beta_for(w, sigma);
+  cudaGetDevice(&p->device);
+  const long long NN = (long long)N * N;
+  const size_t cs = p->precision == FIO_FP64 ? 16 : 8;
+
+  // ---- wedge geometry (host)
+  std::vector<std::vector<std::pair<int, int>>> wp(L);
+  for (int k1 = -N / 2; k1 < N / 2; ++k1)
+    for (int k2 = -N / 2; k2 < N / 2; ++k2) wp[wedge_of(k1, k2, L)].push_back({k1, k2});
+  p->wedges.resize(L);
+  p->rows.clear();
+  p->pt_k1.clear(); p->pt_k2.clear();
+  std::vector<std::vector<int>> x1p(L), x2p(L);
+  for (int l = 0; l < L; ++l) {
+    if (wp[l].empty()) { set_error("empty wedge: L too large for N"); return FIO_EINVAL; }
+    std::vector<RowDev> rows;
+    std::vector<int> k1s, k2s;
+    std::string err;
+    if (!wedge_geometry(wp[l], sigma, w, p->wedges[l], rows, k1s, k2s, x1p[l], x2p[l], err)) {
+      set_error(err);
+      return FIO_EINVAL;
+    }
+    p->wedges[l].row_off = (int)p->rows.size();
+    p->wedges[l].pt_off = (int)p->pt_k1.size();
+    for (auto &rw : rows) {
+      rw.wedge = l;
+      p->max_row_len = std::max(p->max_row_len, rw.len);
+      p->rows.push_back(rw);
+    }
+    p->pt_k1.insert(p->pt_k1.end(), k1s.begin(), k1s.end());
+    p->pt_k2.insert(p->pt_k2.end(), k2s.begin(), k2s.end());
+  }
+
+  // ---- FFT plans and twiddles for every length used
+  std::vector<int> lens = {N};
+  for (auto &wd : p->wedges) { lens.push_back(wd.m1); lens.push_back(wd.m2); }
+  std::sort(lens.begin(), lens.end());
+  lens.erase(std::unique(lens.begin(), lens.end()), lens.end());
+  std::vector<double> tw;
+  p->ffts.clear();
+  for (int n : lens) {
+    FftPlanDev f{};
+    f.n = n;
+    const auto rad = fft_factor(n);
+    if (rad.empty() || (int)rad.size() > kMaxRadixStages || n > kMaxFftLen) {
+      set_error("unsupported FFT length " + std::to_string(n));
+      return FIO_EUNSUPPORTED;
+    }
+    f.nstages = (int)rad.size();
+    for (size_t i = 0; i < rad.size(); ++i) f.radix[i] = rad[i];
+    f.tw_off = (int)(tw.size() / 2);
+    for (int k = 0; k < n; ++k) {
+      tw.push_back(std::cos(2.0 * M_PI * k / n));
+      tw.push_back(-std::sin(2.0 * M_PI * k / n));
+    }
+    p->ffts.push_back(f);
+  }
+  auto fft_index = [&](int n) {
+    for (size_t i = 0; i < p->ffts.size(); ++i)
+      if (p->ffts[i].n == n) return (int)i;
+    return -1;
+  };
+  for (auto &wd : p->wedges) {
+    wd.fft1 = fft_index(wd.m1);
+    wd.fft2 = fft_index(wd.m2);
+    wd.tw1_off = p->ffts[wd.fft1].tw_off;
+    wd.tw2_off = p->ffts[wd.fft2].tw_off;
+  }
+
+  // ---- phase data on the device
+  DevAllocs tmp;
+  PhaseDev ph{};
+  ph.kind = phase->kind;
+  ph.nmodes = phase->kind == FIO_PHASE_TAU_MODES ? phase->nmodes : 0;
+  for (int i = 0; i < nscal; ++i) ph.p[i] = phase->params[i];
+  ph.amp_kind = amp1.kind;
+  ph.a1 = amp1.a1;
+  ph.a2 = amp1.a2;
+  double *d_modes = nullptr;
+  {
+    const int nprm = ph.nmodes ? 5 * ph.nmodes : nscal;
+    std::vector<double> modes(phase->params, phase->params + nprm);
+    fio_status s = upload_tmp(tmp, &d_modes, modes, "upload phase");
+    if (s != FIO_OK) return s;
+  }
+  void *d_xdata = nullptr;
+  FIO_CK(dev_alloc(&d_xdata, plan_xdata_bytes(ph, N)), "alloc phase data");
+  tmp.ptrs.push_back(d_xdata);
+  FIO_CK(plan_xdata(ph, d_modes, N, d_xdata, 0), "phase data kernel");
+
+  // warped points need only the geometry
+  {
+    void *q = nullptr;
+    fio_status s = upload(&q, p->wedges, "upload wedges");
+    p->d_wedges = (WedgeDev *)q;
+    if (s != FIO_OK) return s;
+  }
+  FIO_CK(dev_alloc((void **)&p->d_warp, (size_t)NN * L * sizeof(uint2)), "alloc warp");
+  FIO_CK(plan_warp(ph, d_xdata, N, L, p->d_wedges, p->d_warp, 0), "warp kernel");
+
+  // ---- pass 1: randomized separation rank per wedge (Sec. 3.2)
+  std::vector<std::vector<int>> Csel(L);
+  std::vector<std::vector<cd>> Wmat(L);
+  p->wedge_r.assign(L, 0);
+  double2 *d_AC = nullptr, *d_G = nullptr, *d_part = nullptr;
+  long long ac_cap = 0, g_cap = 0, part_cap = 0;
+  auto nparts_for = [](int r) {
+    const int ntile = (r + 31) / 32;
+    return std::max(1, std::min(1024, 1024 / (ntile * (ntile + 1) / 2)));
+  };
+  auto regrow = [&](double2 **q, long long &cap, long long need, const char *what) -> fio_status {
+    if (need <= cap) return FIO_OK;
+    if (*q) {
+      tmp.ptrs.erase(std::find(tmp.ptrs.begin(), tmp.ptrs.end(), (void *)*q));
+      cudaFree(*q);
+      *q = nullptr;
+      cap = 0;
+    }
+    FIO_CK(dev_alloc((void **)q, (size_t)need * sizeof(double2)), what);
+    tmp.ptrs.push_back(*q);
+    cap = need;
+    return FIO_OK;
+  };
+  auto ensure_ac = [&](int r) -> fio_status {
+    fio_status s = regrow(&d_AC, ac_cap, (long long)r * NN, "alloc A_C");
+    if (s == FIO_OK) s = regrow(&d_G, g_cap, (long long)r * r, "alloc G");
+    if (s == FIO_OK) s = regrow(&d_part, part_cap, (long long)nparts_for(r) * r * r, "alloc Gram partials");
+    return s;
+  };
+  int *d_ck1 = nullptr, *d_ck2 = nullptr;
+  FIO_CK(dev_alloc((void **)&d_ck1, sizeof(int) * rank_cap * 2 + 64), "alloc samples");
+  tmp.ptrs.push_back(d_ck1);
+  d_ck2 = d_ck1 + rank_cap + 16;
+  const int *pk1 = p->pt_k1.data(), *pk2 = p->pt_k2.data();
+
+  auto eval_cols = [&](int l, const std::vector<int> &C) -> fio_status {
+    const WedgeDev &wd = p->wedges[l];
+    const int r = (int)C.size();
+    std::vector<int> c1(r), c2(r);
+    for (int i = 0; i < r; ++i) { c1[i] = pk1[wd.pt_off + C[i]]; c2[i] = pk2[wd.pt_off + C[i]]; }
+    FIO_CK(cudaMemcpy(d_ck1, c1.data(), sizeof(int) * r, cudaMemcpyHostToDevice), "upload C");
+    FIO_CK(cudaMemcpy(d_ck2, c2.data(), sizeof(int) * r, cudaMemcpyHostToDevice), "upload C");
+    fio_status s = ensure_ac(r);
+    if (s != FIO_OK) return s;
+    FIO_CK(plan_eval_cols(ph, d_xdata, N, wd, p->d_warp + (size_t)l * NN, d_ck1, d_ck2, r, d_AC, 0),
+           "A_C kernel");
+    return FIO_OK;
+  };
+
+  for (int l = 0; l < L; ++l) {
+    const int npts = p->wedges[l].npts;
+    int r = std::min({r0, npts, rank_cap});
+    for (int attempt = 0;; ++attempt) {
+      SplitMix64 rng{mix_seed(opt.seed, (uint64_t)l + 1, 2 * (uint64_t)attempt + 1)};
+      std::vector<int> C = sample_distinct(npts, r, rng);
+      fio_status s = eval_cols(l, C);
+      if (s != FIO_OK) return s;
+      FIO_CK(plan_gram(d_AC, NN, r, d_part, nparts_for(r), d_G, 0), "Gram kernel");
+      std::vector<cd> G((size_t)r * r);
+      FIO_CK(cudaMemcpy(G.data(), d_G, sizeof(cd) * r * r, cudaMemcpyDeviceToHost), "download G");
+      std::vector<double> ev;
+      std::vector<cd> V;
+      herm_eig(r, G, ev, V);
+      // singular values of A_C are sqrt(ev); keep s_i > eps s_1 (relative threshold)
+      const double s1 = std::sqrt(std::max(ev[0], 0.0));
+      int q = 0;
+      while (q < r && std::sqrt(std::max(ev[q], 0.0)) > eps * s1) ++q;
+      q = std::max(q, 1);
+      if (3 * q <= r || r == npts) {
+        std::vector<cd> Wm((size_t)r * q);
+        for (int i = 0; i < r; ++i)
+          for (int t = 0; t < q; ++t)
+            Wm[(size_t)i * q + t] = V[(size_t)i * r + t] / std::sqrt(ev[t]);
+        Csel[l] = C;
+        Wmat[l] = Wm;
+        p->wedges[l].q = q;
+        p->wedge_r[l] = r;
+        break;
+      }
+      if (r >= rank_cap) {
+        set_error("separation rank needs more than rank_cap samples in wedge " + std::to_string(l));
+        return FIO_ERANK;
+      }
+      r = std::min({2 * r, rank_cap, npts});
+    }
+  }
+
+  // ---- layout of the factors and grids
+  long long aoff = 0, boff = 0, gunit = 0;
+  for (auto &wd : p->wedges) {
+    wd.alpha_off = aoff;
+    wd.beta_off = boff;
+    wd.grid_unit = gunit;
+    aoff += (long long)wd.q * NN;
+    boff += (long long)wd.q * wd.npts;
+    gunit += (long long)wd.m1 * wd.m2 * wd.q;
+  }
+  p->alpha_elems = aoff;
+  p->beta_elems = boff;
+  p->grid_units = gunit;
+  FIO_CK(dev_alloc(&p->d_alpha, (size_t)aoff * cs), "alloc alpha");
+  FIO_CK(dev_alloc(&p->d_beta, (size_t)boff * cs), "alloc beta");
+  FIO_CK(dev_alloc(&p->d_grid, (size_t)gunit * max_batch * cs), "alloc grids");
+  FIO_CK(dev_alloc(&p->d_fhat, (size_t)NN * max_batch * cs), "alloc spectrum");
+  FIO_CK(cudaMemcpy(p->d_wedges, p->wedges.data(), sizeof(WedgeDev) * L, cudaMemcpyHostToDevice), "upload wedges");
+  {
+    void *q = nullptr;
+    fio_status s = upload(&q, p->rows, "upload rows");
+    p->d_rows = (RowDev *)q;
+    if (s != FIO_OK) return s;
+    s = upload(&q, p->ffts, "upload fft plans");
+    p->d_ffts = (FftPlanDev *)q;
+    if (s != FIO_OK) return s;
+    if (p->precision == FIO_FP64) {
+      s = upload(&p->d_twiddle, tw, "upload twiddles");
+    } else {
+      std::vector<float> twf(tw.begin(), tw.end());
+      s = upload(&p->d_twiddle, twf, "upload twiddles");
+    }
+    if (s != FIO_OK) return s;
+  }
+
+  // ---- pass 2: gamma^x = U (with centre factor and 1/N), gamma^xi = T / phihat
+  double2 *d_W = nullptr, *d_P = nullptr;
+  int *d_rx = nullptr, *d_pk1 = nullptr, *d_pk2 = nullptr;
+  double *d_dec = nullptr;
+  int maxnpts = 0;
+  for (auto &wd : p->wedges) maxnpts = std::max(maxnpts, wd.npts);
+  FIO_CK(dev_alloc((void **)&d_W, sizeof(double2) * (size_t)rank_cap * rank_cap), "alloc W");
+  tmp.ptrs.push_back(d_W);
+  FIO_CK(dev_alloc((void **)&d_P, sizeof(double2) * (size_t)rank_cap * rank_cap), "alloc P");
+  tmp.ptrs.push_back(d_P);
+  FIO_CK(dev_alloc((void **)&d_rx, sizeof(int) * (size_t)rank_cap), "alloc R");
+  tmp.ptrs.push_back(d_rx);
+  FIO_CK(dev_alloc((void **)&d_pk1, sizeof(int) * (size_t)maxnpts * 2), "alloc points");
+  tmp.ptrs.push_back(d_pk1);
+  d_pk2 = d_pk1 + maxnpts;
+  FIO_CK(dev_alloc((void **)&d_dec, sizeof(double) * (size_t)maxnpts), "alloc deconvolution");
+  tmp.ptrs.push_back(d_dec);
+
+  for (int l = 0; l < L; ++l) {
+    const WedgeDev &wd = p->wedges[l];
+    const int r = (int)Csel[l].size(), q = wd.q;
+    fio_status s = eval_cols(l, Csel[l]);
+    if (s != FIO_OK) return s;
+    FIO_CK(cudaMemcpy(d_W, Wmat[l].data(), sizeof(cd) * r * q, cudaMemcpyHostToDevice), "upload W");
+    FIO_CK(plan_form_alpha(d_AC, N, r, q, d_W, wd, p->d_warp + (size_t)l * NN,
+                           (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision, 0),
+           "alpha kernel");
+    // rows R and U_[R] = A_C[R, :] W
+    SplitMix64 rng{mix_seed(opt.seed, (uint64_t)l + 1, 0xA5A5ULL)};
+    const int nr = (int)std::min<long long>(r, NN);
+    std::vector<int> R = sample_distinct((int)NN, nr, rng);
+    std::vector<cd> UR((size_t)nr * q, cd(0)), arow(r);
+    for (int i = 0; i < nr; ++i) {
+      FIO_CK(cudaMemcpy(arow.data(), d_AC + (size_t)R[i] * r, sizeof(cd) * r, cudaMemcpyDeviceToHost),
+             "download A_C row");
+      for (int t = 0; t < q; ++t) {
+        cd acc = 0;
+        for (int c = 0; c < r; ++c) acc += arow[c] * Wmat[l][(size_t)c * q + t];
+        UR[(size_t)i * q + t] = acc;
+      }
+    }
+    // P = U_R^+ through the eigendecomposition of U_R^H U_R, same relative cutoff
+    std::vector<cd> Gq((size_t)q * q, cd(0));
+    for (int a = 0; a < q; ++a)
+      for (int b = 0; b < q; ++b) {
+        cd acc = 0;
+        for (int i = 0; i < nr; ++i) acc += std::conj(UR[(size_t)i * q + a]) * UR[(size_t)i * q + b];
+        Gq[(size_t)a * q + b] = acc;
+      }
+    std::vector<double> evq;
+    std::vector<cd> Q;
+    herm_eig(q, Gq, evq, Q);
+    std::vector<cd> Ginv((size_t)q * q, cd(0));
+    for (int k = 0; k < q; ++k) {
+      if (!(evq[k] > eps * eps * evq[0])) continue;
+      for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b)
+          Ginv[(size_t)a * q + b] += Q[(size_t)a * q + k] * std::conj(Q[(size_t)b * q + k]) / evq[k];
+    }
+    std::vector<cd> P((size_t)q * nr, cd(0));
+    for (int t = 0; t < q; ++t)
+      for (int i = 0; i < nr; ++i) {
+        cd acc = 0;
+        for (int b = 0; b < q; ++b) acc += Ginv[(size_t)t * q + b] * std::conj(UR[(size_t)i * q + b]);
+        P[(size_t)t * nr + i] = acc;
+      }
+    FIO_CK(cudaMemcpy(d_P, P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
+    FIO_CK(cudaMemcpy(d_rx, R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
+    std::vector<double> dec(wd.npts);
+    for (int i = 0; i < wd.npts; ++i)
+      dec[i] = 1.0 / (kb_phihat_host((double)x1p[l][i] / wd.m1, w, p->kb.beta) *
+                      kb_phihat_host((double)x2p[l][i] / wd.m2, w, p->kb.beta));
+    FIO_CK(cudaMemcpy(d_pk1, pk1 + wd.pt_off, sizeof(int) * wd.npts, cudaMemcpyHostToDevice), "upload points");
+    FIO_CK(cudaMemcpy(d_pk2, pk2 + wd.pt_off, sizeof(int) * wd.npts, cudaMemcpyHostToDevice), "upload points");
+    FIO_CK(cudaMemcpy(d_dec, dec.data(), sizeof(double) * wd.npts, cudaMemcpyHostToDevice), "upload deconvolution");
+    FIO_CK(plan_form_beta(ph, d_xdata, N, wd, p->d_warp + (size_t)l * NN, d_rx, nr, q, d_P, d_pk1,
+                          d_pk2, d_dec, (char *)p->d_beta + (size_t)wd.beta_off * cs, p->precision, 0),
+           "beta kernel");
+  }
+  FIO_CK(cudaDeviceSynchronize(), "plan construction");
+
+  // ---- summary
+  p->q_max = 0; p->q_min = 1 << 30; p->r_max = 0;
+  double qs = 0;
+  for (int l = 0; l < L; ++l) {
+    p->q_max = std::max(p->q_max, p->wedges[l].q);
+    p->q_min = std::min(p->q_min, p->wedges[l].q);
+    p->r_max = std::max(p->r_max, p->wedge_r[l]);
+    qs += p->wedges[l].q;
+  }
+  p->q_mean = qs / L;
+  p->bytes_total = (size_t)(aoff + boff) * cs + (size_t)gunit * max_batch * cs +
+                   (size_t)NN * max_batch * cs + (size_t)NN * L * sizeof(uint2) +
+                   tw.size() / 2 * cs + p->rows.size() * sizeof(RowDev) +
+                   p->wedges.size() * sizeof(WedgeDev) + p->ffts.size() * sizeof(FftPlanDev);
+  // algorithmic bytes of one batch-1 apply: input, spectrum (written and read),
+  // output, both factors, warped points, every grid written once and read once
+  p->alg_bytes = (unsigned long long)(4 * NN * cs + (aoff + boff) * cs + NN * L * 8 + 2 * gunit * cs);
+  p->plan_seconds =
+      std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count();
+  return FIO_OK;
+}
+
+}  // namespace fio

@@ -1,0 +1,408 @@
+// plan_kernels.cu -- FP64 device kernels of the preprocessing step (Sec. 3.2):
+// warped points y_l(x) = grad_xi Phi(x, xihat_l) (Sec. 1.4), entries of the
+// residual kernel A_{x,xi} = a(x,xi) exp(2 pi i Phi_l(x,xi)) (Eq. probform) at
+// sampled columns and rows, the Gram matrix of A_[C], and the factors
+// gamma^x = U = A_[C] V S^-1 and gamma^xi = T = U_[R]^+ A_[R].
+//
+// Everything here is double precision: the residual phase cancels O(N) terms
+// (Sec. 1.3), and the warped points are reduced modulo 1 to 32-bit fractions
+// before any lower-precision use.
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "fio_internal.h"
+
+namespace fio {
+
+namespace {
+
+constexpr double kTwoPi = 6.283185307179586476925286766559;
+constexpr int kMmax = 8;              // tau modes: m in [-8, 8]
+constexpr int kNm = 2 * kMmax + 1;
+
+__device__ __forceinline__ int imodp(long long a, int n) {
+  long long r = a % n;
+  return (int)(r < 0 ? r + n : r);
+}
+
+// Per-x phase data: ellipse axes (c1, c2), or the tau modes grouped by m:
+// C_m(x) = sum_{j : m_j = m} a_j exp(i (2 pi k_j.x + p_j)), so that
+// tau(x, theta) = Re sum_m C_m(x) exp(i m theta) (an exact regrouping).
+struct XView {
+  const double2 *ell;   // [x] (c1, c2)
+  const double2 *Cm;    // [x][kNm]
+};
+
+__device__ __forceinline__ XView xview(const PhaseDev &ph, const void *xd) {
+  XView v{nullptr, nullptr};
+  if (ph.kind == FIO_PHASE_ELLIPSE) v.ell = (const double2 *)xd;
+  if (ph.kind == FIO_PHASE_TAU_MODES) v.Cm = (const double2 *)xd;
+  return v;
+}
+
+// sum_m C_m e^{i m theta} and sum_m m C_m e^{i m theta}, with e = e^{i theta}.
+__device__ __forceinline__ void tau_sums(const double2 *C, double ec, double es, double2 &S,
+                                         double2 &Sm) {
+  S = C[kMmax];
+  Sm = make_double2(0.0, 0.0);
+  double pc = 1.0, ps = 0.0;  // e^{i m theta}
+  for (int m = 1; m <= kMmax; ++m) {
+    const double nc = pc * ec - ps * es, ns = pc * es + ps * ec;
+    pc = nc;
+    ps = ns;
+    const double2 Cp = C[kMmax + m], Cn = C[kMmax - m];
+    // C_m e^{i m th} + C_{-m} e^{-i m th}
+    const double2 tp = make_double2(Cp.x * pc - Cp.y * ps, Cp.x * ps + Cp.y * pc);
+    const double2 tn = make_double2(Cn.x * pc + Cn.y * ps, Cn.y * pc - Cn.x * ps);
+    S.x += tp.x + tn.x;
+    S.y += tp.y + tn.y;
+    Sm.x += m * (tp.x - tn.x);
+    Sm.y += m * (tp.y - tn.y);
+  }
+}
+
+// Psi(x, xi) = Phi(x, xi) - x.xi
+__device__ __forceinline__ double psi(const PhaseDev &ph, const XView &xv, long long x, int k1,
+                                      int k2) {
+  if (k1 == 0 && k2 == 0) return 0.0;
+  const double d1 = k1, d2 = k2;
+  const double r = sqrt(d1 * d1 + d2 * d2);
+  switch (ph.kind) {
+    case FIO_PHASE_SHIFT_WAVE:
+      return -(ph.p[0] * d1 + ph.p[1] * d2) + ph.p[2] * r;
+    case FIO_PHASE_ELLIPSE: {
+      const double2 c = xv.ell[x];
+      return sqrt(c.x * c.x * d1 * d1 + c.y * c.y * d2 * d2);
+    }
+    case FIO_PHASE_TAU_MODES: {
+      double2 S, Sm;
+      tau_sums(xv.Cm + x * kNm, d1 / r, d2 / r, S, Sm);
+      return r * S.x;
+    }
+  }
+  return 0.0;
+}
+
+// grad_xi Psi at the unit vector (ct, st).
+__device__ __forceinline__ void grad_psi_unit(const PhaseDev &ph, const XView &xv, long long x,
+                                              double ct, double st, double &g1, double &g2) {
+  switch (ph.kind) {
+    case FIO_PHASE_SHIFT_WAVE:
+      g1 = -ph.p[0] + ph.p[2] * ct;
+      g2 = -ph.p[1] + ph.p[2] * st;
+      return;
+    case FIO_PHASE_ELLIPSE: {
+      const double2 c = xv.ell[x];
+      const double a = c.x * c.x, b = c.y * c.y;
+      const double rho = sqrt(a * ct * ct + b * st * st);
+      g1 = a * ct / rho;
+      g2 = b * st / rho;
+      return;
+    }
+    case FIO_PHASE_TAU_MODES: {
+      // grad(|xi| tau) = tau xihat + (d tau / d theta) xihat_perp
+      double2 S, Sm;
+      tau_sums(xv.Cm + x * kNm, ct, st, S, Sm);
+      const double tau = S.x, dtau = -Sm.y;  // Re(i sum m C_m e^{i m th}) = -Im(sum m ...)
+      g1 = tau * ct - dtau * st;
+      g2 = tau * st + dtau * ct;
+      return;
+    }
+  }
+  g1 = g2 = 0.0;
+}
+
+__device__ __forceinline__ double amp(const PhaseDev &ph, double x1, int k1, int k2) {
+  if (ph.amp_kind != FIO_AMP_SEPARABLE) return 1.0;
+  const double r = sqrt((double)k1 * k1 + (double)k2 * k2);
+  const double cth = r > 0 ? k1 / r : 1.0;
+  return (1.0 + ph.a1 * sinpi(2.0 * x1)) * (1.0 + ph.a2 * cth);
+}
+
+// A_{x,xi} = a(x,xi) exp(2 pi i [Phi(x,xi) - y'.(M xi)]) with y' the 32-bit
+// fraction Y / 2^32 (its integer part only adds integers to the phase).
+// x.xi mod 1 and y'.(M xi) mod 1 are formed exactly in integer arithmetic.
+__device__ __forceinline__ double2 entry(const PhaseDev &ph, const XView &xv, int N,
+                                         const WedgeDev &w, long long x, uint2 Y, int k1,
+                                         int k2) {
+  const int n1 = (int)(x / N), n2 = (int)(x % N);
+  const int xx = imodp((long long)n1 * k1 + (long long)n2 * k2, N);
+  const int kk1 = w.M[0] * k1 + w.M[1] * k2, kk2 = w.M[2] * k1 + w.M[3] * k2;
+  const uint32_t yk = Y.x * (uint32_t)kk1 + Y.y * (uint32_t)kk2;  // mod 2^32
+  const double frac = (double)xx / N - (double)yk * 2.3283064365386962890625e-10;
+  const double phase = frac + psi(ph, xv, x, k1, k2);
+  double s, c;
+  sincospi(2.0 * phase, &s, &c);
+  const double a = amp(ph, (double)n1 / N, k1, k2);
+  return make_double2(a * c, a * s);
+}
+
+// ------------------------------------------------------------------ kernels --
+
+__global__ void k_xdata(PhaseDev ph, const double *__restrict__ modes, int N, void *xd) {
+  const long long NN = (long long)N * N;
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= NN) return;
+  const double x1 = (double)(x / N) / N, x2 = (double)(x % N) / N;
+  if (ph.kind == FIO_PHASE_ELLIPSE) {
+    double2 c;
+    c.x = ph.p[0] + ph.p[1] * sinpi(2.0 * x1) * sinpi(2.0 * x2);
+    c.y = ph.p[2] + ph.p[3] * cospi(2.0 * x1) * cospi(2.0 * x2);
+    ((double2 *)xd)[x] = c;
+  } else if (ph.kind == FIO_PHASE_TAU_MODES) {
+    double2 C[kNm];
+    for (int m = 0; m < kNm; ++m) C[m] = make_double2(0.0, 0.0);
+    for (int j = 0; j < ph.nmodes; ++j) {
+      const double *p = modes + 5 * j;
+      const int m = (int)llrint(p[3]);
+      double s, c;
+      sincos(kTwoPi * (p[1] * x1 + p[2] * x2) + p[4], &s, &c);
+      C[m + kMmax].x += p[0] * c;
+      C[m + kMmax].y += p[0] * s;
+    }
+    double2 *out = (double2 *)xd + x * kNm;
+    for (int m = 0; m < kNm; ++m) out[m] = C[m];
+  }
+}
+
+__global__ void k_warp(PhaseDev ph, const void *xd, int N, int L, const WedgeDev *__restrict__ W,
+                       uint2 *__restrict__ warp) {
+  const long long NN = (long long)N * N;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NN * L) return;
+  const int l = (int)(idx / NN);
+  const long long x = idx % NN;
+  const WedgeDev w = W[l];
+  const XView xv = xview(ph, xd);
+  double st, ct;
+  sincospi(2.0 * l / L, &st, &ct);  // xihat_l = (cos 2 pi l / L, sin 2 pi l / L)
+  double g1, g2;
+  grad_psi_unit(ph, xv, x, ct, st, g1, g2);
+  const double y1 = (double)(x / N) / N + g1, y2 = (double)(x % N) / N + g2;
+  // y'.xi'' = y.xi with xi = Minv xi''  =>  y' = Minv^T y
+  const double yp[2] = {w.Minv[0] * y1 + w.Minv[2] * y2, w.Minv[1] * y1 + w.Minv[3] * y2};
+  uint32_t Y[2];
+  for (int d = 0; d < 2; ++d) {
+    const double f = yp[d] - floor(yp[d]);
+    const double s = rint(f * 4294967296.0);
+    Y[d] = s >= 4294967296.0 ? 0u : (uint32_t)s;
+  }
+  warp[idx] = make_uint2(Y[0], Y[1]);
+}
+
+__global__ void k_eval_cols(PhaseDev ph, const void *xd, int N, WedgeDev w,
+                            const uint2 *__restrict__ warp_l, const int *__restrict__ ck1,
+                            const int *__restrict__ ck2, int r, double2 *__restrict__ AC) {
+  const long long NN = (long long)N * N;
+  const long long idx = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= NN * r) return;
+  const long long x = idx / r;
+  const int c = (int)(idx % r);
+  AC[idx] = entry(ph, xview(ph, xd), N, w, x, warp_l[x], ck1[c], ck2[c]);
+}
+
+// Gram of A (rows x r): upper tiles of 32 x 32 over row chunks (partials),
+// then an ordered sum over chunks (deterministic).
+constexpr int kGT = 32, kGR = 32;
+
+__global__ void __launch_bounds__(256) k_gram_partial(const double2 *__restrict__ A,
+                                                      long long rows, int r, int ntile,
+                                                      double2 *__restrict__ partial,
+                                                      int nparts) {
+  __shared__ double2 Ai[kGR][kGT], Aj[kGR][kGT];
+  int tile = blockIdx.x, bi = 0;
+  while (tile >= ntile - bi) {
+    tile -= ntile - bi;
+    ++bi;
+  }
+  const int bj = bi + tile;
+  const int part = blockIdx.y;
+  const long long chunk = (rows + nparts - 1) / nparts;
+  const long long r0 = part * chunk, r1 = min(rows, r0 + chunk);
+  const int ti = threadIdx.x / 8, tj = (threadIdx.x % 8) * 4;
+  double2 acc[4];
+  for (int k = 0; k < 4; ++k) acc[k] = make_double2(0.0, 0.0);
+  for (long long rb = r0; rb < r1; rb += kGR) {
+    for (int e = threadIdx.x; e < kGR * kGT; e += blockDim.x) {
+      const int rr = e / kGT, cc = e % kGT;
+      const long long row = rb + rr;
+      const int ci = bi * kGT + cc, cj = bj * kGT + cc;
+      Ai[rr][cc] = (row < r1 && ci < r) ? A[row * r + ci] : make_double2(0.0, 0.0);
+      Aj[rr][cc] = (row < r1 && cj < r) ? A[row * r + cj] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    for (int rr = 0; rr < kGR; ++rr) {
+      const double2 a = Ai[rr][ti];
+      for (int k = 0; k < 4; ++k) {
+        const double2 b = Aj[rr][tj + k];
+        acc[k].x += a.x * b.x + a.y * b.y;  // conj(a) b
+        acc[k].y += a.x * b.y - a.y * b.x;
+      }
+    }
+    __syncthreads();
+  }
+  const int i = bi * kGT + ti;
+  for (int k = 0; k < 4; ++k) {
+    const int j = bj * kGT + tj + k;
+    if (i < r && j < r) partial[(long long)part * r * r + (long long)i * r + j] = acc[k];
+  }
+}
+
+__global__ void k_gram_reduce(const double2 *__restrict__ partial, int nparts, int r,
+                              double2 *__restrict__ G) {
+  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  if (idx >= r * r) return;
+  const int i = idx / r, j = idx % r;
+  if (j < i || (j / kGT) < (i / kGT)) return;
+  double2 s = make_double2(0.0, 0.0);
+  for (int p = 0; p < nparts; ++p) {
+    const double2 v = partial[(long long)p * r * r + idx];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  G[i * r + j] = s;
+  G[j * r + i] = make_double2(s.x, -s.y);
+}
+
+template <typename C>
+__device__ __forceinline__ void store_c(void *base, long long i, double2 v) {
+  if constexpr (sizeof(C) == 8) ((float2 *)base)[i] = make_float2((float)v.x, (float)v.y);
+  else ((double2 *)base)[i] = v;
+}
+
+template <typename C>
+__global__ void k_form_alpha(const double2 *__restrict__ AC, int N, int r, int q,
+                             const double2 *__restrict__ Wm, WedgeDev w,
+                             const uint2 *__restrict__ warp_l, void *alpha_l) {
+  const long long NN = (long long)N * N;
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= NN) return;
+  // centre-frequency factor exp(2 pi i y'.xi_c) / N (Sec. 3.4), exact mod 1
+  const uint2 Y = warp_l[x];
+  const uint32_t yk = Y.x * (uint32_t)w.xc1 + Y.y * (uint32_t)w.xc2;
+  double s, c;
+  sincospi(2.0 * ((double)yk * 2.3283064365386962890625e-10), &s, &c);
+  const double invN = 1.0 / N;
+  const double2 ctr = make_double2(c * invN, s * invN);
+  const double2 *row = AC + x * r;
+  for (int t = 0; t < q; ++t) {
+    double2 acc = make_double2(0.0, 0.0);
+    for (int k = 0; k < r; ++k) {
+      const double2 a = row[k], b = Wm[k * q + t];
+      acc.x += a.x * b.x - a.y * b.y;
+      acc.y += a.x * b.y + a.y * b.x;
+    }
+    const double2 v = make_double2(acc.x * ctr.x - acc.y * ctr.y, acc.x * ctr.y + acc.y * ctr.x);
+    store_c<C>(alpha_l, t * NN + x, v);
+  }
+}
+
+constexpr int kBetaChunk = 16;
+
+template <typename C>
+__global__ void k_form_beta(PhaseDev ph, const void *xd, int N, WedgeDev w,
+                            const uint2 *__restrict__ warp_l, const int *__restrict__ rx, int r,
+                            int q, const double2 *__restrict__ P, const int *__restrict__ pk1,
+                            const int *__restrict__ pk2, const double *__restrict__ dec,
+                            void *beta_l) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= w.npts) return;
+  const XView xv = xview(ph, xd);
+  const int k1 = pk1[p], k2 = pk2[p];
+  const double d = dec[p];
+  for (int t0 = 0; t0 < q; t0 += kBetaChunk) {
+    double2 acc[kBetaChunk];
+#pragma unroll
+    for (int k = 0; k < kBetaChunk; ++k) acc[k] = make_double2(0.0, 0.0);
+    for (int i = 0; i < r; ++i) {
+      const long long x = rx[i];
+      const double2 a = entry(ph, xv, N, w, x, warp_l[x], k1, k2);
+#pragma unroll
+      for (int k = 0; k < kBetaChunk; ++k) {
+        if (t0 + k < q) {
+          const double2 b = P[(long long)(t0 + k) * r + i];
+          acc[k].x += b.x * a.x - b.y * a.y;
+          acc[k].y += b.x * a.y + b.y * a.x;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < kBetaChunk; ++k)
+      if (t0 + k < q)
+        store_c<C>(beta_l, (long long)(t0 + k) * w.npts + p,
+                   make_double2(acc[k].x * d, acc[k].y * d));
+  }
+}
+
+unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+size_t plan_xdata_bytes(const PhaseDev &ph, int N) {
+  const size_t NN = (size_t)N * N;
+  if (ph.kind == FIO_PHASE_ELLIPSE) return NN * sizeof(double2);
+  if (ph.kind == FIO_PHASE_TAU_MODES) return NN * kNm * sizeof(double2);
+  return 16;
+}
+
+cudaError_t plan_xdata(const PhaseDev &ph, const double *d_modes, int N, void *d_xdata,
+                       cudaStream_t s) {
+  const long long NN = (long long)N * N;
+  k_xdata<<<blocks(NN, 256), 256, 0, s>>>(ph, d_modes, N, d_xdata);
+  return cudaGetLastError();
+}
+
+cudaError_t plan_warp(const PhaseDev &ph, const void *d_xdata, int N, int L, const WedgeDev *d_w,
+                      uint2 *d_warp, cudaStream_t s) {
+  const long long n = (long long)N * N * L;
+  k_warp<<<blocks(n, 256), 256, 0, s>>>(ph, d_xdata, N, L, d_w, d_warp);
+  return cudaGetLastError();
+}
+
+cudaError_t plan_eval_cols(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
+                           const uint2 *d_warp_l, const int *d_ck1, const int *d_ck2, int r,
+                           double2 *d_AC, cudaStream_t s) {
+  const long long n = (long long)N * N * r;
+  k_eval_cols<<<blocks(n, 256), 256, 0, s>>>(ph, d_xdata, N, w, d_warp_l, d_ck1, d_ck2, r, d_AC);
+  return cudaGetLastError();
+}
+
+cudaError_t plan_gram(const double2 *d_AC, long long rows, int r, double2 *d_partial, int nparts,
+                      double2 *d_G, cudaStream_t s) {
+  const int ntile = (r + kGT - 1) / kGT;
+  const int ntiles = ntile * (ntile + 1) / 2;
+  k_gram_partial<<<dim3(ntiles, nparts), 256, 0, s>>>(d_AC, rows, r, ntile, d_partial, nparts);
+  k_gram_reduce<<<blocks((long long)r * r, 256), 256, 0, s>>>(d_partial, nparts, r, d_G);
+  return cudaGetLastError();
+}
+
+cudaError_t plan_form_alpha(const double2 *d_AC, int N, int r, int q, const double2 *d_W,
+                            const WedgeDev &w, const uint2 *d_warp_l, void *d_alpha_l,
+                            int precision, cudaStream_t s) {
+  const long long NN = (long long)N * N;
+  if (precision == FIO_FP64)
+    k_form_alpha<double2><<<blocks(NN, 256), 256, 0, s>>>(d_AC, N, r, q, d_W, w, d_warp_l,
+                                                          d_alpha_l);
+  else
+    k_form_alpha<float2><<<blocks(NN, 256), 256, 0, s>>>(d_AC, N, r, q, d_W, w, d_warp_l,
+                                                         d_alpha_l);
+  return cudaGetLastError();
+}
+
+cudaError_t plan_form_beta(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
+                           const uint2 *d_warp_l, const int *d_rx, int r, int q,
+                           const double2 *d_P, const int *d_pk1, const int *d_pk2,
+                           const double *d_dec, void *d_beta_l, int precision, cudaStream_t s) {
+  if (precision == FIO_FP64)
+    k_form_beta<double2><<<blocks(w.npts, 128), 128, 0, s>>>(ph, d_xdata, N, w, d_warp_l, d_rx,
+                                                             r, q, d_P, d_pk1, d_pk2, d_dec,
+                                                             d_beta_l);
+  else
+    k_form_beta<float2><<<blocks(w.npts, 128), 128, 0, s>>>(ph, d_xdata, N, w, d_warp_l, d_rx, r,
+                                                            q, d_P, d_pk1, d_pk2, d_dec,
+                                                            d_beta_l);
+  return cudaGetLastError();
+}
+
+}  // namespace fio

@@ -1,0 +1,306 @@
+"""Python binding of libfio.so (include/fio.h): argument marshalling only.
+
+Every step of the apply path runs in the library's CUDA kernels; PyTorch only
+supplies device memory and the current stream.  There is no CPU fallback: if
+the library is missing, every call raises ``FioError``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libfio.so")
+
+FIO_OK, FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ERANK, FIO_ETIMEOUT, FIO_EUNSUPPORTED = range(7)
+PHASE_SHIFT_WAVE, PHASE_ELLIPSE, PHASE_TAU_MODES = 0, 1, 2
+AMP_ONE, AMP_SEPARABLE = 0, 1
+MIXED, FP64 = 0, 1
+
+
+class FioError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"{msg} (status {status})")
+        self.status = status
+
+
+class _Phase(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("nmodes", ctypes.c_int),
+                ("params", ctypes.POINTER(ctypes.c_double))]
+
+
+class _Amp(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("a1", ctypes.c_double), ("a2", ctypes.c_double)]
+
+
+class _Options(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("L", ctypes.c_int), ("sigma", ctypes.c_double),
+                ("kb_width", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("r0", ctypes.c_int),
+                ("rank_cap", ctypes.c_int), ("max_batch", ctypes.c_int)]
+
+
+class _PlanInfo(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_int), ("L", ctypes.c_int), ("precision", ctypes.c_int),
+                ("kb_width", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("sigma", ctypes.c_double), ("kb_beta", ctypes.c_double), ("eps", ctypes.c_double),
+                ("q_max", ctypes.c_int), ("q_min", ctypes.c_int), ("r_max", ctypes.c_int),
+                ("q_mean", ctypes.c_double),
+                ("bytes_alpha", ctypes.c_ulonglong), ("bytes_beta", ctypes.c_ulonglong),
+                ("bytes_warp", ctypes.c_ulonglong), ("bytes_grid", ctypes.c_ulonglong),
+                ("bytes_total", ctypes.c_ulonglong), ("grid_points", ctypes.c_ulonglong),
+                ("alg_bytes_apply", ctypes.c_ulonglong), ("plan_seconds", ctypes.c_double)]
+
+
+class _WedgeInfo(ctypes.Structure):
+    _fields_ = [("M", ctypes.c_int * 4), ("xc1", ctypes.c_int), ("xc2", ctypes.c_int),
+                ("b1", ctypes.c_int), ("n1", ctypes.c_int), ("b2", ctypes.c_int),
+                ("n2", ctypes.c_int), ("m1", ctypes.c_int), ("m2", ctypes.c_int),
+                ("q", ctypes.c_int), ("r", ctypes.c_int), ("npts", ctypes.c_int)]
+
+
+# Every symbol include/fio.h declares (checked by the tests).
+EXPORTS = [
+    "fio_options_default", "fio_plan_create", "fio_apply", "fio_apply_adjoint", "fio_plan_sync",
+    "fio_plan_get_info", "fio_plan_get_wedge", "fio_plan_export_wedge", "fio_plan_export_warp",
+    "fio_plan_destroy",
+    "fio_dft2", "fio_default_wedges", "fio_wedge_map", "fio_wedge_geometry", "fio_kb_eval",
+    "fio_kb_width_for", "fio_host_eigh", "fio_status_string", "fio_last_error", "fio_version",
+]
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded libfio.so; raises FioError if it has not been built."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise FioError(-1, f"{LIB_PATH} is missing: build it with __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+            L.fio_options_default.argtypes = [ctypes.POINTER(_Options)]
+            L.fio_plan_create.argtypes = [I, ctypes.POINTER(_Phase), ctypes.POINTER(_Amp), D,
+                                          ctypes.POINTER(_Options), ctypes.POINTER(P)]
+            L.fio_apply.argtypes = [P, P, P, I, P]
+            L.fio_apply_adjoint.argtypes = [P, P, P, I, P]
+            L.fio_plan_sync.argtypes = [P, P]
+            L.fio_plan_get_info.argtypes = [P, ctypes.POINTER(_PlanInfo)]
+            L.fio_plan_get_wedge.argtypes = [P, I, ctypes.POINTER(_WedgeInfo)]
+            L.fio_plan_export_wedge.argtypes = [P, I, P, P, P, P]
+            L.fio_plan_export_warp.argtypes = [P, I, P]
+            L.fio_plan_destroy.argtypes = [P]
+            L.fio_plan_destroy.restype = None
+            L.fio_dft2.argtypes = [I, I, P, P, I, I, P]
+            L.fio_default_wedges.argtypes = [I]
+            L.fio_wedge_map.argtypes = [I, I, P]
+            L.fio_wedge_geometry.argtypes = [I, I, D, I, I, ctypes.POINTER(_WedgeInfo)]
+            L.fio_kb_eval.argtypes = [I, D, I, P, P, P, P]
+            L.fio_kb_width_for.argtypes = [D]
+            L.fio_host_eigh.argtypes = [I, P, P, P]
+            L.fio_status_string.restype = ctypes.c_char_p
+            L.fio_status_string.argtypes = [I]
+            L.fio_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def _check(status: int, what: str):
+    if status != FIO_OK:
+        detail = lib().fio_last_error().decode(errors="replace")
+        raise FioError(status, f"{what}: {detail}")
+
+
+def _np_ptr(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream_ptr(torch, device):
+    return ctypes.c_void_p(torch.cuda.current_stream(device).cuda_stream)
+
+
+def _wedge_dict(w: _WedgeInfo) -> dict:
+    return {"M": list(w.M), "xc": (w.xc1, w.xc2), "b1": w.b1, "n1": w.n1, "b2": w.b2, "n2": w.n2,
+            "m1": w.m1, "m2": w.m2, "q": w.q, "r": w.r, "npts": w.npts}
+
+
+class Plan:
+    """fio_plan_create / fio_apply / fio_apply_adjoint for one operator L.
+
+    phase: one of PHASE_* with ``params`` (shift/wave: [x01, x02, c]; ellipse:
+    [A1, B1, A2, B2]; tau modes: [K, 5] rows {a, k1, k2, m, p}).
+    amp: None (a = 1) or (a1, a2) for a = (1 + a1 sin 2 pi x1)(1 + a2 cos theta).
+    """
+
+    def __init__(self, N: int, phase: int, params, eps: float, amp=None, precision: str = "mixed",
+                 L: int = 0, sigma: float = 0.0, kb_width: int = 0, seed: int = 0x5EED5EED,
+                 r0: int = 0, rank_cap: int = 0, max_batch: int = 1, device=None):
+        import torch
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self._handle = ctypes.c_void_p()
+        prm = np.ascontiguousarray(np.asarray(params, dtype=np.float64).ravel())
+        self._params = prm
+        ph = _Phase(int(phase), len(prm) // 5 if phase == PHASE_TAU_MODES else 0,
+                    prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        am = _Amp(AMP_ONE, 0.0, 0.0) if amp is None else _Amp(AMP_SEPARABLE, float(amp[0]),
+                                                            float(amp[1]))
+        opt = _Options()
+        lib().fio_options_default(ctypes.byref(opt))
+        opt.precision = FP64 if precision in ("fp64", FP64) else MIXED
+        opt.L, opt.sigma, opt.kb_width = int(L), float(sigma), int(kb_width)
+        opt.seed, opt.r0, opt.rank_cap, opt.max_batch = int(seed), int(r0), int(rank_cap), int(max_batch)
+        self.N = int(N)
+        self.precision = opt.precision
+        self.max_batch = max(1, int(max_batch))
+        with torch.cuda.device(self.device):
+            _check(lib().fio_plan_create(self.N, ctypes.byref(ph), ctypes.byref(am), float(eps),
+                                         ctypes.byref(opt), ctypes.byref(self._handle)),
+                   "fio_plan_create")
+        self.dtype = torch.complex128 if self.precision == FP64 else torch.complex64
+
+    # -- lifetime
+    def close(self):
+        if getattr(self, "_handle", None) and self._handle.value:
+            lib().fio_plan_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+    # -- apply
+    def _prep(self, x):
+        torch = self._torch
+        if not isinstance(x, torch.Tensor) or x.device != self.device:
+            raise FioError(FIO_EINVAL, f"input must be a tensor on {self.device}")
+        if x.dtype != self.dtype:
+            raise FioError(FIO_EINVAL, f"input dtype must be {self.dtype}, got {x.dtype}")
+        if x.shape[-2:] != (self.N, self.N):
+            raise FioError(FIO_EINVAL, f"input must end with ({self.N}, {self.N})")
+        return x.contiguous()
+
+    def _run(self, fn, x, out, what):
+        torch = self._torch
+        x = self._prep(x)
+        batch = x.numel() // (self.N * self.N)
+        if out is None:
+            out = torch.empty_like(x)
+        elif out.shape != x.shape or out.dtype != x.dtype or not out.is_contiguous():
+            raise FioError(FIO_EINVAL, "out must be a contiguous tensor like the input")
+        _check(fn(self._handle, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                  int(batch), _stream_ptr(torch, self.device)), what)
+        return out
+
+    def apply(self, f, out=None):
+        """out = L f (fio_apply); f: complex tensor [..., N, N] on the plan's device."""
+        return self._run(lib().fio_apply, f, out, "fio_apply")
+
+    def adjoint(self, g, out=None):
+        """out = L* g (fio_apply_adjoint)."""
+        return self._run(lib().fio_apply_adjoint, g, out, "fio_apply_adjoint")
+
+    def sync(self):
+        _check(lib().fio_plan_sync(self._handle, _stream_ptr(self._torch, self.device)),
+               "fio_plan_sync")
+
+    # -- introspection
+    def info(self) -> dict:
+        i = _PlanInfo()
+        _check(lib().fio_plan_get_info(self._handle, ctypes.byref(i)), "fio_plan_get_info")
+        return {k: getattr(i, k) for k, _ in _PlanInfo._fields_}
+
+    def wedge(self, l: int) -> dict:
+        w = _WedgeInfo()
+        _check(lib().fio_plan_get_wedge(self._handle, int(l), ctypes.byref(w)), "fio_plan_get_wedge")
+        return _wedge_dict(w)
+
+    def export_wedge(self, l: int):
+        """(alpha [q, N, N], beta [q, npts], k1 [npts], k2 [npts]) of wedge l, complex128."""
+        w = self.wedge(l)
+        q, n = w["q"], w["npts"]
+        alpha = np.empty((q, self.N, self.N), np.complex128)
+        beta = np.empty((q, n), np.complex128)
+        k1 = np.empty(n, np.int32)
+        k2 = np.empty(n, np.int32)
+        _check(lib().fio_plan_export_wedge(self._handle, int(l), _np_ptr(alpha), _np_ptr(beta),
+                                           _np_ptr(k1), _np_ptr(k2)), "fio_plan_export_wedge")
+        return alpha, beta, k1, k2
+
+    def export_warp(self, l: int) -> np.ndarray:
+        """Warped points of wedge l: [N, N, 2] fractions y' = M^-T grad Phi mod 1."""
+        y = np.empty((self.N, self.N, 2), np.float64)
+        _check(lib().fio_plan_export_warp(self._handle, int(l), _np_ptr(y)), "fio_plan_export_warp")
+        return y
+
+
+def dft2(x, inverse: bool = False, out=None):
+    """Unitary 2D DFT of Eq. dft on the GPU (fio_dft2); spectrum in centred order."""
+    import torch
+    if x.dtype not in (torch.complex64, torch.complex128) or not x.is_cuda:
+        raise FioError(FIO_EINVAL, "dft2 needs a complex CUDA tensor")
+    x = x.contiguous()
+    N = x.shape[-1]
+    if out is None:
+        out = torch.empty_like(x)
+    prec = FP64 if x.dtype == torch.complex128 else MIXED
+    _check(lib().fio_dft2(N, prec, ctypes.c_void_p(x.data_ptr()), ctypes.c_void_p(out.data_ptr()),
+                          x.numel() // (N * N), int(bool(inverse)), _stream_ptr(torch, x.device)),
+           "fio_dft2")
+    return out
+
+
+# ---------------------------------------------------------------- host utils --
+
+def default_wedges(N: int) -> int:
+    return lib().fio_default_wedges(int(N))
+
+
+def kb_width_for(eps: float) -> int:
+    return lib().fio_kb_width_for(float(eps))
+
+
+def wedge_map(N: int, L: int) -> np.ndarray:
+    out = np.empty((N, N), np.int32)
+    _check(lib().fio_wedge_map(int(N), int(L), _np_ptr(out)), "fio_wedge_map")
+    return out
+
+
+def wedge_geometry(N: int, L: int, sigma: float, kb_width: int, l: int) -> dict:
+    w = _WedgeInfo()
+    _check(lib().fio_wedge_geometry(int(N), int(L), float(sigma), int(kb_width), int(l),
+                                    ctypes.byref(w)), "fio_wedge_geometry")
+    return _wedge_dict(w)
+
+
+def kb_eval(w: int, beta: float, s=None, nu=None):
+    s = np.ascontiguousarray(np.zeros(0) if s is None else s, np.float64)
+    nu = np.ascontiguousarray(np.zeros(len(s)) if nu is None else nu, np.float64)
+    n = max(len(s), len(nu))
+    if len(s) < n:
+        s = np.zeros(n)
+    phi, phihat = np.empty(n), np.empty(n)
+    _check(lib().fio_kb_eval(int(w), float(beta), n, _np_ptr(s), _np_ptr(phi), _np_ptr(nu),
+                             _np_ptr(phihat)), "fio_kb_eval")
+    return phi, phihat
+
+
+def host_eigh(A: np.ndarray):
+    A = np.ascontiguousarray(A, np.complex128)
+    n = A.shape[0]
+    ev = np.empty(n)
+    V = np.empty((n, n), np.complex128)
+    _check(lib().fio_host_eigh(n, _np_ptr(A), _np_ptr(ev), _np_ptr(V)), "fio_host_eigh")
+    return ev, V

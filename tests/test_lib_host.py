@@ -1,0 +1,189 @@
+"""CPU tests of the C-ABI library: it loads, exports what include/fio.h declares,
+and its host logic (wedges of Sec. 1.3, boxes of Sec. 3.4, Kaiser-Bessel kernel,
+Hermitian eigensolver of Sec. 3.2, argument checks) is right.  No CUDA call."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def fio():
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_math_0610051_gb300 import fio
+    return fio
+
+
+def _declared():
+    with open(os.path.join(ROOT, "include", "fio.h")) as fh:
+        src = fh.read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(fio_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_exports_every_declared_symbol(fio):
+    lib = fio.lib()
+    names = _declared()
+    assert len(names) >= 20
+    for n in names:
+        assert hasattr(lib, n), n
+    assert sorted(fio.EXPORTS) == names
+
+
+def test_version_and_status_strings(fio):
+    lib = fio.lib()
+    assert lib.fio_version() >= 100
+    for s in range(7):
+        assert lib.fio_status_string(s)
+
+
+def test_default_wedges(fio):
+    assert [fio.default_wedges(N) for N in (64, 256, 512, 1024)] == [8, 16, 24, 32]
+
+
+def test_kb_width_rule(fio):
+    assert fio.kb_width_for(1e-4) == 6
+    assert fio.kb_width_for(1e-6) == 8
+
+
+@pytest.mark.parametrize("N,L", [(64, 8), (128, 16), (256, 16), (512, 24)])
+def test_wedge_partition(fio, N, L):
+    """W_l = {(2l-1) pi/L <= arg xi < (2l+1) pi/L}: every xi in exactly one wedge, by angle."""
+    wm = fio.wedge_map(N, L)
+    k = np.arange(N) - N // 2
+    K1, K2 = np.meshgrid(k, k, indexing="ij")
+    th = np.mod(np.arctan2(K2, K1) + np.pi / L, 2 * np.pi)
+    expect = np.floor(th / (2 * np.pi / L)).astype(int) % L
+    expect[N // 2, N // 2] = 0
+    assert np.array_equal(wm, expect)
+    counts = np.bincount(wm.ravel(), minlength=L)
+    assert counts.sum() == N * N and counts.min() > 0.5 * N * N / L
+
+
+@pytest.mark.parametrize("N,L", [(64, 8), (256, 16), (1024, 32)])
+def test_wedge_boxes(fio, N, L):
+    """Sec. 3.4: xi' = M xi - xi_c maps the wedge into its box; M unimodular; grid >= sigma * box."""
+    wm = fio.wedge_map(N, L)
+    k = np.arange(N) - N // 2
+    K1, K2 = np.meshgrid(k, k, indexing="ij")
+    sigma, w = 2.0, 6
+    total = 0
+    for l in range(L):
+        g = fio.wedge_geometry(N, L, sigma, w, l)
+        M = np.array(g["M"]).reshape(2, 2)
+        assert round(np.linalg.det(M)) == 1
+        sel = wm == l
+        pts = np.stack([K1[sel], K2[sel]])
+        xp = M @ pts - np.array(g["xc"])[:, None]
+        assert xp[0].min() == g["b1"] and xp[0].max() == g["b1"] + g["n1"] - 1
+        assert xp[1].min() == g["b2"] and xp[1].max() == g["b2"] + g["n2"] - 1
+        assert len({(a, b) for a, b in xp.T}) == g["npts"] == sel.sum()
+        for m, n in ((g["m1"], g["n1"]), (g["m2"], g["n2"])):
+            assert m >= sigma * n and m % 2 == 0
+            r = m
+            for p in (2, 3, 5):
+                while r % p == 0:
+                    r //= p
+            assert r == 1
+        total += g["n1"] * g["n2"]
+    if N == 1024:
+        # the sheared boxes cover about 2.9 N^2 frequencies in total
+        assert total < 3.2 * N * N
+
+
+def test_kb_kernel_matches_bessel_and_quadrature(fio):
+    """phi(s) = I0(beta sqrt(1-(2s/w)^2))/I0(beta); phihat is its Fourier transform."""
+    from scipy import integrate, special
+    w, beta = 6, 13.855
+    s = np.linspace(-3.2, 3.2, 41)
+    phi, _ = fio.kb_eval(w, beta, s=s)
+    z = 1 - (2 * s / w) ** 2
+    ref = np.where(z > 0, special.i0(beta * np.sqrt(np.maximum(z, 0))) / special.i0(beta), 0)
+    assert np.max(np.abs(phi - ref)) < 1e-13
+    nu = np.array([0.0, 0.05, 0.1, 0.2, 0.25, 0.4, 0.7, 1.2])
+    _, ph = fio.kb_eval(w, beta, nu=nu)
+    for v, got in zip(nu, ph):
+        f = lambda t: special.i0(beta * np.sqrt(max(1 - (2 * t / w) ** 2, 0))) / special.i0(beta) \
+            * np.cos(2 * np.pi * v * t)
+        q, _ = integrate.quad(f, -w / 2, w / 2, limit=200, epsabs=1e-14, epsrel=1e-13)
+        assert abs(got - q) < 1e-10 * max(1.0, abs(q)), (v, got, q)
+
+
+@pytest.mark.parametrize("eps", [1e-4, 1e-6])
+def test_kb_nufft_accuracy(fio, eps):
+    """The default width/shape for eps gives a 1D type-2 NUFFT error below eps / 5
+    (sigma = 2), measured against the direct sum."""
+    w = fio.kb_width_for(eps)
+    g = np.random.default_rng(1)
+    n, m = 120, 240
+    k = np.arange(-n // 2, n // 2)
+    F = g.standard_normal(n) + 1j * g.standard_normal(n)
+    y = g.uniform(0, 1, 800)
+    exact = np.exp(2j * np.pi * np.outer(y, k)) @ F
+    _, ph = fio.kb_eval(w, 0.0, nu=k / m)
+    G = np.zeros(m, complex)
+    G[k % m] = F / ph
+    Gg = np.fft.ifft(G) * m
+    u = y * m
+    j0 = np.floor(u - w / 2).astype(int) + 1
+    res = np.zeros_like(exact)
+    for a in range(w):
+        j = j0 + a
+        phi, _ = fio.kb_eval(w, 0.0, s=u - j)
+        res += phi * Gg[j % m]
+    err = np.linalg.norm(res - exact) / np.linalg.norm(exact)
+    assert err < eps / 5, err
+
+
+@pytest.mark.parametrize("n", [1, 5, 24, 70])
+def test_host_eigh_matches_numpy(fio, n):
+    g = np.random.default_rng(n)
+    X = g.standard_normal((n, n)) + 1j * g.standard_normal((n, n))
+    A = X @ X.conj().T
+    ev, V = fio.host_eigh(A)
+    ref = np.sort(np.linalg.eigvalsh(A))[::-1]
+    assert np.max(np.abs(ev - ref)) < 1e-11 * ref[0]
+    assert np.max(np.abs(V.conj().T @ V - np.eye(n))) < 1e-11
+    assert np.max(np.abs(A @ V - V * ev)) < 1e-10 * ref[0]
+
+
+def test_host_eigh_rank_deficient(fio):
+    """A Gram matrix of rank 3 (the situation of oversampled columns, Sec. 3.2)."""
+    g = np.random.default_rng(7)
+    B = g.standard_normal((40, 3)) + 1j * g.standard_normal((40, 3))
+    A = B.conj().T @ B
+    A = np.pad(A, ((0, 9), (0, 9)))
+    C = g.standard_normal((12, 12)) + 1j * g.standard_normal((12, 12))
+    Q, _ = np.linalg.qr(C)
+    A = Q @ A @ Q.conj().T
+    ev, V = fio.host_eigh(A)
+    assert np.all(ev[3:] < 1e-12 * ev[0])
+    assert np.max(np.abs(A @ V[:, :3] - V[:, :3] * ev[:3])) < 1e-10 * ev[0]
+
+
+def test_plan_create_rejects_bad_arguments_before_cuda(fio):
+    """Argument errors are reported before any CUDA call (FIO_EINVAL), with a message."""
+    lib = fio.lib()
+    prm = np.array([2 / 3, 1 / 3, 2 / 3, 1 / 3])
+    bad = np.array([np.nan, 0, 1, 0])
+    tau = np.array([[0.1, 1, 0, 2.5, 0.0]])
+
+    def create(N, params, kind=fio.PHASE_ELLIPSE, eps=1e-4, nmodes=0):
+        ph = fio._Phase(kind, nmodes, params.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+        h = ctypes.c_void_p()
+        st = lib.fio_plan_create(N, ctypes.byref(ph), None, eps, None, ctypes.byref(h))
+        return st, h.value
+
+    assert create(63, prm) == (fio.FIO_EINVAL, None)
+    assert create(4, prm) == (fio.FIO_EINVAL, None)
+    assert create(64, prm, eps=0.5)[0] == fio.FIO_EINVAL
+    assert create(64, bad)[0] == fio.FIO_EINVAL
+    assert b"non-finite" in lib.fio_last_error()
+    assert create(64, tau.ravel().copy(), fio.PHASE_TAU_MODES, nmodes=1)[0] == fio.FIO_EINVAL
+    assert lib.fio_apply(None, None, None, 1, None) == fio.FIO_EINVAL
+    assert lib.fio_dft2(100 + 14, 0, None, None, 1, 0, None) == fio.FIO_EINVAL
