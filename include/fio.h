@@ -143,6 +143,9 @@ typedef struct {
   unsigned long long grid_points;   /* sum over wedges of m1*m2*q (one input) */
   unsigned long long alg_bytes_apply; /* algorithmic HBM bytes of one batch-1 apply */
   double plan_seconds;              /* wall time of fio_plan_create */
+  double sep_error;                 /* largest per-wedge estimate of the relative Frobenius
+                                       error of the separated factors (Sec. 4, Table 1's
+                                       estimator over every column, on 200 random rows) */
 } fio_plan_info;
 
 /* Plan summary (host struct filled). */

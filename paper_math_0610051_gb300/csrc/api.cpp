@@ -154,6 +154,7 @@ fio_status fio_plan_get_info(fio_plan p, fio_plan_info *info) {
   info->grid_points = (unsigned long long)p->grid_units;
   info->alg_bytes_apply = p->alg_bytes;
   info->plan_seconds = p->plan_seconds;
+  info->sep_error = p->sep_err;
   return FIO_OK;
 }
 

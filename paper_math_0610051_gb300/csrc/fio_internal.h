@@ -68,6 +68,7 @@ struct fio_plan_s {
   double eps = 0, sigma = 2.0, plan_seconds = 0;
   fio::KbParams kb{};
   int q_max = 0, q_min = 0, r_max = 0;
+  double sep_err = 0;
   double q_mean = 0;
   int device = 0;
 
@@ -76,6 +77,7 @@ struct fio_plan_s {
   std::vector<fio::RowDev> rows;
   std::vector<fio::FftPlanDev> ffts;
   std::vector<int> wedge_r;
+  std::vector<double> wedge_err;   // separation error estimate per wedge
   std::vector<int> pt_k1, pt_k2;   // every frequency, wedge by wedge, row-major in each box
   long long grid_units = 0;        // sum_l m1 m2 q
   long long alpha_elems = 0, beta_elems = 0;
@@ -150,5 +152,17 @@ cudaError_t plan_form_beta(const PhaseDev &ph, const void *d_xdata, int N, const
                            const uint2 *d_warp_l, const int *d_rx, int r, int q,
                            const double2 *d_P, const int *d_pk1, const int *d_pk2,
                            const double *d_dec, void *d_beta_l, int precision, cudaStream_t s);
+
+// Per-column squared error of U T against A on s sampled rows (validation).
+cudaError_t plan_validate(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
+                          const uint2 *d_warp_l, const int *d_gx, int s, const double2 *d_UG,
+                          const double2 *d_T, int q, const int *d_pk1, const int *d_pk2,
+                          double *d_err, double *d_nrm, cudaStream_t st);
+
+// Per-column squared error of U T against A on s sampled rows (validation).
+cudaError_t plan_validate(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
+                          const uint2 *d_warp_l, const int *d_gx, int s, const double2 *d_UG,
+                          const double2 *d_T, int q, const int *d_pk1, const int *d_pk2,
+                          double *d_err, double *d_nrm, cudaStream_t st);
 
 }  // namespace fio

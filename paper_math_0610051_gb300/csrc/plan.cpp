@@ -25,6 +25,16 @@ namespace fio {
 
 using cd = std::complex<double>;
 
+// Separation rule (Sec. 3.2 with a stricter acceptance test): singular values
+// of A_[C] above kSvdFraction * eps * s_1 are kept; a sample is accepted when
+// q <= r/3 and the relative Frobenius error of U T, measured on
+// kValidationRows fresh random rows against every column of the wedge, is at
+// most kValidationTarget * eps.  Otherwise the worst-fitted columns join the
+// next sample and r doubles.
+constexpr double kSvdFraction = 0.25;
+constexpr double kValidationTarget = 0.5;
+constexpr int kValidationRows = 200;
+
 // ------------------------------------------------------------- FFT sizes --
 
 std::vector<int> fft_factor(int n) {
@@ -489,8 +499,6 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   FIO_CK(plan_warp(ph, d_xdata, N, L, p->d_wedges, p->d_warp, 0), "warp kernel");
 
   // ---- pass 1: randomized separation rank per wedge (Sec. 3.2)
-  std::vector<std::vector<int>> Csel(L);
-  std::vector<std::vector<cd>> Wmat(L);
   p->wedge_r.assign(L, 0);
   double2 *d_AC = nullptr, *d_G = nullptr, *d_part = nullptr;
   long long ac_cap = 0, g_cap = 0, part_cap = 0;
@@ -537,40 +545,183 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     return FIO_OK;
   };
 
+  // per-wedge scratch of the separation
+  int maxnpts = 0;
+  for (auto &wd : p->wedges) maxnpts = std::max(maxnpts, wd.npts);
+  const int s_val = (int)std::min<long long>(kValidationRows, NN);
+  int *d_pk1 = nullptr, *d_pk2 = nullptr, *d_rx = nullptr, *d_gx = nullptr;
+  double *d_err = nullptr, *d_nrm = nullptr;
+  double2 *d_W = nullptr, *d_P = nullptr, *d_UG = nullptr, *d_T = nullptr;
+  long long T_cap = 0;
+  auto scratch = [&](void **q, size_t bytes, const char *what) -> fio_status {
+    FIO_CK(dev_alloc(q, bytes), what);
+    tmp.ptrs.push_back(*q);
+    return FIO_OK;
+  };
+  {
+    fio_status s = FIO_OK;
+    if (s == FIO_OK) s = scratch((void **)&d_pk1, sizeof(int) * (size_t)maxnpts * 2, "alloc points");
+    if (s == FIO_OK) s = scratch((void **)&d_err, sizeof(double) * (size_t)maxnpts * 2, "alloc validation");
+    if (s == FIO_OK) s = scratch((void **)&d_rx, sizeof(int) * (size_t)(4 * rank_cap + kValidationRows), "alloc rows");
+    if (s == FIO_OK) s = scratch((void **)&d_W, sizeof(double2) * (size_t)rank_cap * rank_cap, "alloc W");
+    if (s == FIO_OK) s = scratch((void **)&d_P, sizeof(double2) * (size_t)rank_cap * 4 * rank_cap, "alloc P");
+    if (s == FIO_OK) s = scratch((void **)&d_UG, sizeof(double2) * (size_t)kValidationRows * rank_cap, "alloc U rows");
+    if (s != FIO_OK) return s;
+  }
+  d_pk2 = d_pk1 + maxnpts;
+  d_nrm = d_err + maxnpts;
+  d_gx = d_rx + 4 * rank_cap;
+
+  // rows X of U = A_C W (A_C on the device, [x][c]); W is r x q
+  auto u_rows = [&](const std::vector<int> &X, int r, int q, const std::vector<cd> &W,
+                    std::vector<cd> &out) -> fio_status {
+    out.assign(X.size() * (size_t)q, cd(0));
+    std::vector<cd> arow(r);
+    for (size_t i = 0; i < X.size(); ++i) {
+      FIO_CK(cudaMemcpy(arow.data(), d_AC + (size_t)X[i] * r, sizeof(cd) * r, cudaMemcpyDeviceToHost),
+             "download A_C row");
+      for (int t = 0; t < q; ++t) {
+        cd acc = 0;
+        for (int c = 0; c < r; ++c) acc += arow[c] * W[(size_t)c * q + t];
+        out[i * q + t] = acc;
+      }
+    }
+    return FIO_OK;
+  };
+  // P = U_R^+ (q x nr) through the eigendecomposition of U_R^H U_R, relative cutoff
+  auto pinv = [&](const std::vector<cd> &UR, int nr, int q, double cut) {
+    std::vector<cd> Gq((size_t)q * q, cd(0));
+    for (int a = 0; a < q; ++a)
+      for (int b = 0; b < q; ++b) {
+        cd acc = 0;
+        for (int i = 0; i < nr; ++i) acc += std::conj(UR[(size_t)i * q + a]) * UR[(size_t)i * q + b];
+        Gq[(size_t)a * q + b] = acc;
+      }
+    std::vector<double> evq;
+    std::vector<cd> Q;
+    herm_eig(q, Gq, evq, Q);
+    std::vector<cd> Ginv((size_t)q * q, cd(0));
+    for (int k = 0; k < q; ++k) {
+      if (!(evq[k] > cut * cut * evq[0])) continue;
+      for (int a = 0; a < q; ++a)
+        for (int b = 0; b < q; ++b)
+          Ginv[(size_t)a * q + b] += Q[(size_t)a * q + k] * std::conj(Q[(size_t)b * q + k]) / evq[k];
+    }
+    std::vector<cd> P((size_t)q * nr, cd(0));
+    for (int t = 0; t < q; ++t)
+      for (int i = 0; i < nr; ++i) {
+        cd acc = 0;
+        for (int b = 0; b < q; ++b) acc += Ginv[(size_t)t * q + b] * std::conj(UR[(size_t)i * q + b]);
+        P[(size_t)t * nr + i] = acc;
+      }
+    return P;
+  };
+
+  struct Sep {
+    std::vector<int> C, R;
+    std::vector<cd> W, P;
+    int q = 0;
+    double est = 0;
+  };
+  std::vector<Sep> sep(L);
+  p->wedge_err.assign(L, 0.0);
+  const double svd_cut = kSvdFraction * eps;
   for (int l = 0; l < L; ++l) {
-    const int npts = p->wedges[l].npts;
+    const WedgeDev &wd = p->wedges[l];
+    const int npts = wd.npts;
+    FIO_CK(cudaMemcpy(d_pk1, pk1 + wd.pt_off, sizeof(int) * npts, cudaMemcpyHostToDevice), "upload points");
+    FIO_CK(cudaMemcpy(d_pk2, pk2 + wd.pt_off, sizeof(int) * npts, cudaMemcpyHostToDevice), "upload points");
+    std::vector<int> anchors;  // columns kept from earlier attempts (worst fitted)
     int r = std::min({r0, npts, rank_cap});
     for (int attempt = 0;; ++attempt) {
-      SplitMix64 rng{mix_seed(opt.seed, (uint64_t)l + 1, 2 * (uint64_t)attempt + 1)};
-      std::vector<int> C = sample_distinct(npts, r, rng);
+      // C: the anchors plus uniform random columns (Sec. 3.2, step 1)
+      SplitMix64 rng{mix_seed(opt.seed, (uint64_t)l + 1, 3 * (uint64_t)attempt + 1)};
+      if ((int)anchors.size() > r) anchors.resize(r);
+      std::vector<int> C = anchors;
+      std::unordered_set<int> have(C.begin(), C.end());
+      for (int c : sample_distinct(npts, std::min(npts, r), rng))
+        if ((int)C.size() < r && have.insert(c).second) C.push_back(c);
+      while ((int)C.size() < r) {
+        const int c = (int)rng.below((uint64_t)npts);
+        if (have.insert(c).second) C.push_back(c);
+      }
+      std::sort(C.begin(), C.end());
+      const int rc = (int)C.size();
+      // SVD of A_[C] through its Gram matrix (step 2)
       fio_status s = eval_cols(l, C);
       if (s != FIO_OK) return s;
-      FIO_CK(plan_gram(d_AC, NN, r, d_part, nparts_for(r), d_G, 0), "Gram kernel");
-      std::vector<cd> G((size_t)r * r);
-      FIO_CK(cudaMemcpy(G.data(), d_G, sizeof(cd) * r * r, cudaMemcpyDeviceToHost), "download G");
+      FIO_CK(plan_gram(d_AC, NN, rc, d_part, nparts_for(rc), d_G, 0), "Gram kernel");
+      std::vector<cd> G((size_t)rc * rc);
+      FIO_CK(cudaMemcpy(G.data(), d_G, sizeof(cd) * rc * rc, cudaMemcpyDeviceToHost), "download G");
       std::vector<double> ev;
       std::vector<cd> V;
-      herm_eig(r, G, ev, V);
-      // singular values of A_C are sqrt(ev); keep s_i > eps s_1 (relative threshold)
+      herm_eig(rc, G, ev, V);
       const double s1 = std::sqrt(std::max(ev[0], 0.0));
       int q = 0;
-      while (q < r && std::sqrt(std::max(ev[q], 0.0)) > eps * s1) ++q;
+      while (q < rc && std::sqrt(std::max(ev[q], 0.0)) > svd_cut * s1) ++q;
       q = std::max(q, 1);
-      if (3 * q <= r || r == npts) {
-        std::vector<cd> Wm((size_t)r * q);
-        for (int i = 0; i < r; ++i)
-          for (int t = 0; t < q; ++t)
-            Wm[(size_t)i * q + t] = V[(size_t)i * r + t] / std::sqrt(ev[t]);
-        Csel[l] = C;
-        Wmat[l] = Wm;
+      std::vector<cd> Wm((size_t)rc * q);
+      for (int i = 0; i < rc; ++i)
+        for (int t = 0; t < q; ++t) Wm[(size_t)i * q + t] = V[(size_t)i * rc + t] / std::sqrt(ev[t]);
+      // rows R and T = U_[R]^+ A_[R] (steps 3-4)
+      SplitMix64 rr{mix_seed(opt.seed, (uint64_t)l + 1, 3 * (uint64_t)attempt + 2)};
+      const int nr = (int)std::min<long long>(NN, std::max(rc, 4 * q));
+      std::vector<int> R = sample_distinct((int)NN, nr, rr);
+      std::vector<cd> UR;
+      if ((s = u_rows(R, rc, q, Wm, UR)) != FIO_OK) return s;
+      std::vector<cd> P = pinv(UR, nr, q, svd_cut);
+      FIO_CK(cudaMemcpy(d_P, P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
+      FIO_CK(cudaMemcpy(d_rx, R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
+      if ((s = regrow(&d_T, T_cap, (long long)q * npts, "alloc T")) != FIO_OK) return s;
+      FIO_CK(plan_form_beta(ph, d_xdata, N, wd, p->d_warp + (size_t)l * NN, d_rx, nr, q, d_P, d_pk1,
+                            d_pk2, nullptr, d_T, FIO_FP64, 0),
+             "T kernel");
+      // validation on fresh rows against every column of the wedge
+      SplitMix64 rg{mix_seed(opt.seed, (uint64_t)l + 1, 3 * (uint64_t)attempt + 3)};
+      std::vector<int> Gx = sample_distinct((int)NN, s_val, rg);
+      std::vector<cd> UG;
+      if ((s = u_rows(Gx, rc, q, Wm, UG)) != FIO_OK) return s;
+      FIO_CK(cudaMemcpy(d_UG, UG.data(), sizeof(cd) * UG.size(), cudaMemcpyHostToDevice), "upload U rows");
+      FIO_CK(cudaMemcpy(d_gx, Gx.data(), sizeof(int) * s_val, cudaMemcpyHostToDevice), "upload rows");
+      FIO_CK(plan_validate(ph, d_xdata, N, wd, p->d_warp + (size_t)l * NN, d_gx, s_val, d_UG, d_T, q,
+                           d_pk1, d_pk2, d_err, d_nrm, 0),
+             "validation kernel");
+      std::vector<double> err(npts), nrm(npts);
+      FIO_CK(cudaMemcpy(err.data(), d_err, sizeof(double) * npts, cudaMemcpyDeviceToHost), "download");
+      FIO_CK(cudaMemcpy(nrm.data(), d_nrm, sizeof(double) * npts, cudaMemcpyDeviceToHost), "download");
+      double se = 0, sn = 0;
+      for (int i = 0; i < npts; ++i) { se += err[i]; sn += nrm[i]; }
+      const double est = std::sqrt(se / std::max(sn, 1e-300));
+      const bool ok = (est <= kValidationTarget * eps && 3 * q <= rc) || rc >= npts;
+      if (ok || rc >= rank_cap) {
+        if (!ok && est > eps) {
+          set_error("wedge " + std::to_string(l) + ": separation error " + std::to_string(est) +
+                    " above eps with rank_cap samples");
+          return FIO_ERANK;
+        }
+        sep[l].C = C;
+        sep[l].R = R;
+        sep[l].W = Wm;
+        sep[l].P = P;
+        sep[l].q = q;
+        sep[l].est = est;
         p->wedges[l].q = q;
-        p->wedge_r[l] = r;
+        p->wedge_r[l] = rc;
+        p->wedge_err[l] = est;
         break;
       }
-      if (r >= rank_cap) {
-        set_error("separation rank needs more than rank_cap samples in wedge " + std::to_string(l));
-        return FIO_ERANK;
-      }
+      // pivot: keep the worst-fitted columns for the next, doubled sample
+      std::vector<int> order(npts);
+      std::iota(order.begin(), order.end(), 0);
+      std::sort(order.begin(), order.end(), [&](int a, int b) { return err[a] > err[b]; });
+      const int add = std::max(1, rc / 4);
+      std::unordered_set<int> inC(C.begin(), C.end()), inA(anchors.begin(), anchors.end());
+      int added = 0;
+      for (int i = 0; i < npts && added < add; ++i)
+        if (!inC.count(order[i]) && inA.insert(order[i]).second) {
+          anchors.push_back(order[i]);
+          ++added;
+        }
       r = std::min({2 * r, rank_cap, npts});
     }
   }
@@ -611,73 +762,23 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   }
 
   // ---- pass 2: gamma^x = U (with centre factor and 1/N), gamma^xi = T / phihat
-  double2 *d_W = nullptr, *d_P = nullptr;
-  int *d_rx = nullptr, *d_pk1 = nullptr, *d_pk2 = nullptr;
   double *d_dec = nullptr;
-  int maxnpts = 0;
-  for (auto &wd : p->wedges) maxnpts = std::max(maxnpts, wd.npts);
-  FIO_CK(dev_alloc((void **)&d_W, sizeof(double2) * (size_t)rank_cap * rank_cap), "alloc W");
-  tmp.ptrs.push_back(d_W);
-  FIO_CK(dev_alloc((void **)&d_P, sizeof(double2) * (size_t)rank_cap * rank_cap), "alloc P");
-  tmp.ptrs.push_back(d_P);
-  FIO_CK(dev_alloc((void **)&d_rx, sizeof(int) * (size_t)rank_cap), "alloc R");
-  tmp.ptrs.push_back(d_rx);
-  FIO_CK(dev_alloc((void **)&d_pk1, sizeof(int) * (size_t)maxnpts * 2), "alloc points");
-  tmp.ptrs.push_back(d_pk1);
-  d_pk2 = d_pk1 + maxnpts;
-  FIO_CK(dev_alloc((void **)&d_dec, sizeof(double) * (size_t)maxnpts), "alloc deconvolution");
-  tmp.ptrs.push_back(d_dec);
-
+  {
+    fio_status s = scratch((void **)&d_dec, sizeof(double) * (size_t)maxnpts, "alloc deconvolution");
+    if (s != FIO_OK) return s;
+  }
   for (int l = 0; l < L; ++l) {
     const WedgeDev &wd = p->wedges[l];
-    const int r = (int)Csel[l].size(), q = wd.q;
-    fio_status s = eval_cols(l, Csel[l]);
+    const Sep &sp = sep[l];
+    const int rc = (int)sp.C.size(), q = sp.q, nr = (int)sp.R.size();
+    fio_status s = eval_cols(l, sp.C);
     if (s != FIO_OK) return s;
-    FIO_CK(cudaMemcpy(d_W, Wmat[l].data(), sizeof(cd) * r * q, cudaMemcpyHostToDevice), "upload W");
-    FIO_CK(plan_form_alpha(d_AC, N, r, q, d_W, wd, p->d_warp + (size_t)l * NN,
+    FIO_CK(cudaMemcpy(d_W, sp.W.data(), sizeof(cd) * rc * q, cudaMemcpyHostToDevice), "upload W");
+    FIO_CK(plan_form_alpha(d_AC, N, rc, q, d_W, wd, p->d_warp + (size_t)l * NN,
                            (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision, 0),
            "alpha kernel");
-    // rows R and U_[R] = A_C[R, :] W
-    SplitMix64 rng{mix_seed(opt.seed, (uint64_t)l + 1, 0xA5A5ULL)};
-    const int nr = (int)std::min<long long>(r, NN);
-    std::vector<int> R = sample_distinct((int)NN, nr, rng);
-    std::vector<cd> UR((size_t)nr * q, cd(0)), arow(r);
-    for (int i = 0; i < nr; ++i) {
-      FIO_CK(cudaMemcpy(arow.data(), d_AC + (size_t)R[i] * r, sizeof(cd) * r, cudaMemcpyDeviceToHost),
-             "download A_C row");
-      for (int t = 0; t < q; ++t) {
-        cd acc = 0;
-        for (int c = 0; c < r; ++c) acc += arow[c] * Wmat[l][(size_t)c * q + t];
-        UR[(size_t)i * q + t] = acc;
-      }
-    }
-    // P = U_R^+ through the eigendecomposition of U_R^H U_R, same relative cutoff
-    std::vector<cd> Gq((size_t)q * q, cd(0));
-    for (int a = 0; a < q; ++a)
-      for (int b = 0; b < q; ++b) {
-        cd acc = 0;
-        for (int i = 0; i < nr; ++i) acc += std::conj(UR[(size_t)i * q + a]) * UR[(size_t)i * q + b];
-        Gq[(size_t)a * q + b] = acc;
-      }
-    std::vector<double> evq;
-    std::vector<cd> Q;
-    herm_eig(q, Gq, evq, Q);
-    std::vector<cd> Ginv((size_t)q * q, cd(0));
-    for (int k = 0; k < q; ++k) {
-      if (!(evq[k] > eps * eps * evq[0])) continue;
-      for (int a = 0; a < q; ++a)
-        for (int b = 0; b < q; ++b)
-          Ginv[(size_t)a * q + b] += Q[(size_t)a * q + k] * std::conj(Q[(size_t)b * q + k]) / evq[k];
-    }
-    std::vector<cd> P((size_t)q * nr, cd(0));
-    for (int t = 0; t < q; ++t)
-      for (int i = 0; i < nr; ++i) {
-        cd acc = 0;
-        for (int b = 0; b < q; ++b) acc += Ginv[(size_t)t * q + b] * std::conj(UR[(size_t)i * q + b]);
-        P[(size_t)t * nr + i] = acc;
-      }
-    FIO_CK(cudaMemcpy(d_P, P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
-    FIO_CK(cudaMemcpy(d_rx, R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
+    FIO_CK(cudaMemcpy(d_P, sp.P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
+    FIO_CK(cudaMemcpy(d_rx, sp.R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
     std::vector<double> dec(wd.npts);
     for (int i = 0; i < wd.npts; ++i)
       dec[i] = 1.0 / (kb_phihat_host((double)x1p[l][i] / wd.m1, w, p->kb.beta) *
@@ -701,6 +802,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     qs += p->wedges[l].q;
   }
   p->q_mean = qs / L;
+  p->sep_err = 0;
+  for (double e : p->wedge_err) p->sep_err = std::max(p->sep_err, e);
   p->bytes_total = (size_t)(aoff + boff) * cs + (size_t)gunit * max_batch * cs +
                    (size_t)NN * max_batch * cs + (size_t)NN * L * sizeof(uint2) +
                    tw.size() / 2 * cs + p->rows.size() * sizeof(RowDev) +

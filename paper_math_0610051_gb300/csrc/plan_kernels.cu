@@ -310,7 +310,7 @@ __global__ void k_form_beta(PhaseDev ph, const void *xd, int N, WedgeDev w,
   if (p >= w.npts) return;
   const XView xv = xview(ph, xd);
   const int k1 = pk1[p], k2 = pk2[p];
-  const double d = dec[p];
+  const double d = dec ? dec[p] : 1.0;
   for (int t0 = 0; t0 < q; t0 += kBetaChunk) {
     double2 acc[kBetaChunk];
 #pragma unroll
@@ -335,9 +335,48 @@ __global__ void k_form_beta(PhaseDev ph, const void *xd, int N, WedgeDev w,
   }
 }
 
+// Column-wise error of the separated factors on s sampled rows (the
+// estimator of Sec. 4, Table 1, taken over every column of the wedge):
+// err[p] = sum_i |A(x_i, xi_p) - sum_t U[i][t] T[t][p]|^2, nrm[p] = sum_i |A|^2.
+__global__ void k_validate(PhaseDev ph, const void *xd, int N, WedgeDev w,
+                           const uint2 *__restrict__ warp_l, const int *__restrict__ gx, int s,
+                           const double2 *__restrict__ UG, const double2 *__restrict__ T, int q,
+                           const int *__restrict__ pk1, const int *__restrict__ pk2,
+                           double *__restrict__ err, double *__restrict__ nrm) {
+  const int p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= w.npts) return;
+  const XView xv = xview(ph, xd);
+  const int k1 = pk1[p], k2 = pk2[p];
+  double e = 0.0, n = 0.0;
+  for (int i = 0; i < s; ++i) {
+    const long long x = gx[i];
+    const double2 a = entry(ph, xv, N, w, x, warp_l[x], k1, k2);
+    double2 u = make_double2(0.0, 0.0);
+    for (int t = 0; t < q; ++t) {
+      const double2 b = UG[(long long)i * q + t], c = T[(long long)t * w.npts + p];
+      u.x += b.x * c.x - b.y * c.y;
+      u.y += b.x * c.y + b.y * c.x;
+    }
+    const double dx = a.x - u.x, dy = a.y - u.y;
+    e += dx * dx + dy * dy;
+    n += a.x * a.x + a.y * a.y;
+  }
+  err[p] = e;
+  nrm[p] = n;
+}
+
 unsigned blocks(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
+
+cudaError_t plan_validate(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
+                          const uint2 *d_warp_l, const int *d_gx, int s, const double2 *d_UG,
+                          const double2 *d_T, int q, const int *d_pk1, const int *d_pk2,
+                          double *d_err, double *d_nrm, cudaStream_t st) {
+  k_validate<<<blocks(w.npts, 128), 128, 0, st>>>(ph, d_xdata, N, w, d_warp_l, d_gx, s, d_UG, d_T,
+                                                  q, d_pk1, d_pk2, d_err, d_nrm);
+  return cudaGetLastError();
+}
 
 size_t plan_xdata_bytes(const PhaseDev &ph, int N) {
   const size_t NN = (size_t)N * N;

@@ -51,7 +51,8 @@ class _PlanInfo(ctypes.Structure):
                 ("bytes_alpha", ctypes.c_ulonglong), ("bytes_beta", ctypes.c_ulonglong),
                 ("bytes_warp", ctypes.c_ulonglong), ("bytes_grid", ctypes.c_ulonglong),
                 ("bytes_total", ctypes.c_ulonglong), ("grid_points", ctypes.c_ulonglong),
-                ("alg_bytes_apply", ctypes.c_ulonglong), ("plan_seconds", ctypes.c_double)]
+                ("alg_bytes_apply", ctypes.c_ulonglong), ("plan_seconds", ctypes.c_double),
+                ("sep_error", ctypes.c_double)]
 
 
 class _WedgeInfo(ctypes.Structure):
