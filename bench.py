@@ -1,0 +1,427 @@
+#!/usr/bin/env python
+"""Throughput of the wedge-factorised FIO apply on GB300.
+
+Workload: the ellipse phase Phi = x.xi + sqrt(c1^2 xi1^2 + c2^2 xi2^2),
+c1 = (2 + sin 2pi x1 sin 2pi x2)/3, c2 = (2 + cos 2pi x1 cos 2pi x2)/3, a = 1,
+N = 1024, separation threshold eps = 1e-4, mixed precision (complex64 NUFFT and
+FFT, FP64 plan), a batch of B white-noise inputs resident in HBM.  One step is
+one pass of the whole hot path: fio_apply (S0-S3) on the batch and
+fio_apply_adjoint (S4) on a second batch; it produces 2 B N^2 FIO outputs.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Under torchrun every rank runs its own replica on its own GPU (weak scaling,
+no data-path collective); rank 0 prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "FIO outputs/s at N=1024, rel-L2<=1e-4 (mixed vs FP64 path), % HBM roofline"
+UNIT = "outputs/s"
+FALLBACK_HBM_GBS = 6800.0
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
+KERNEL_SRC = os.path.join(ROOT, "paper_math_0610051_gb300", "csrc", "apply.cu")
+
+
+def log(*a):
+    print(*a, file=sys.stderr, flush=True)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=40)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--N", type=int, default=1024)
+    ap.add_argument("--batch", type=int, default=8)
+    ap.add_argument("--eps", type=float, default=1e-4)
+    ap.add_argument("--no-fp64", action="store_true", help="skip the FP64-path comparison")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle baseline")
+    return ap.parse_args()
+
+
+def workload_name(a):
+    return (f"ellipse phase (c1,c2 = (2 + sin.sin)/3, (2 + cos.cos)/3), a=1, N={a.N}, "
+            f"eps={a.eps:g}, batch of {a.batch} white-noise inputs, apply + adjoint")
+
+
+# ------------------------------------------------------------------ helpers --
+
+def dist_setup():
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    return world, rank, local
+
+
+def allreduce(x, op="max"):
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()):
+        return x
+    t = torch.tensor([float(x)], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX if op == "max" else dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def barrier():
+    import torch.distributed as dist
+    if dist.is_available() and dist.is_initialized():
+        dist.barrier()
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as fh:
+            d = json.load(fh)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_sha():
+    with open(KERNEL_SRC, "rb") as fh:
+        return hashlib.sha256(fh.read()).hexdigest()[:16]
+
+
+def recorded_traffic(kernel, batch, N):
+    """Per-launch DRAM bytes of `kernel` from the committed ncu summary, if the
+    kernel source is unchanged since the capture (else None)."""
+    try:
+        with open(TRAFFIC_FILE) as fh:
+            d = json.load(fh)
+        e = d[kernel]
+        if e["source_sha"] != kernel_sha() or e["N"] != N:
+            return None
+        return float(e["bytes_per_input"]) * batch + float(e.get("bytes_fixed", 0.0))
+    except Exception:
+        return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    NAMES = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.out = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "100", "-i", str(self.idx)], stdout=self.out, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.out.flush()
+        with open(self.out.name) as fh:
+            rows = [r.strip().split(", ") for r in fh if r.strip()]
+        os.unlink(self.out.name)
+        sm, mx, reasons = [], [], set()
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                mx.append(float(r[2]))
+            except (ValueError, IndexError):
+                continue
+            for name, v in zip(self.NAMES, r[5:9]):
+                if v.strip().lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "samples": len(sm),
+                "reasons": sorted(reasons)}
+
+
+def stage_bytes(plan, B):
+    """Algorithmic HBM bytes of each stage for one launch on B inputs (complex64)."""
+    info = plan.info()
+    N, L = info["N"], info["L"]
+    cs = 16 if plan.precision == 1 else 8
+    NN = N * N
+    ws = [plan.wedge(l) for l in range(L)]
+    grid = sum(w["m1"] * w["m2"] * w["q"] for w in ws) * B * cs
+    half = sum(w["n1"] * w["m2"] * w["q"] for w in ws) * B * cs
+    runs = sum(w["npts"] * w["q"] for w in ws) * B * cs
+    io = B * NN * cs
+    a, wp, bt = info["bytes_alpha"], info["bytes_warp"], info["bytes_beta"]
+    return {
+        "S0_dft": 2 * io, "S1_scatter": io + bt + half, "S2_colfft": half + grid,
+        "S3_interp": a + wp + grid + io, "S4a_spread": io + a + wp + grid,
+        "S4b_colfft": grid + half, "S4b_rowfft": half + runs, "S4c_gather": runs + bt + io,
+        "S4d_idft": 2 * io,
+    }
+
+
+# -------------------------------------------------------------- CPU oracle --
+
+def cpu_oracle_rate(N, f0, budget_s=15.0, out0=None):
+    """Forward direct sums of the oracle (FP64, all host threads) on a bounded
+    sample of output points, the input DFT included.  Returns (outputs/s,
+    threads, points, rel-L2 of out0 at those points or None)."""
+    from oracle import oracle as orc
+    from paper_math_0610051_gb300 import synth
+    ph = orc.Phase(orc.ELLIPSE, synth.ellipse_params())
+    amp = orc.Amplitude()
+    t0 = time.perf_counter()
+    fh = orc.dft2(f0)
+    t_dft = time.perf_counter() - t0
+    n1, n2 = synth.sample_points(N, 32, seed=99)
+    t0 = time.perf_counter()
+    orc.apply_points(ph, amp, fh, n1, n2)
+    per_pt = (time.perf_counter() - t0) / 32
+    s = int(max(64, min(8192, (budget_s - t_dft) / per_pt)))
+    n1, n2 = synth.sample_points(N, s, seed=7)
+    t0 = time.perf_counter()
+    ref = orc.apply_points(ph, amp, fh, n1, n2)
+    t_pts = time.perf_counter() - t0
+    err = orc.rel_l2(ref, out0[n1, n2]) if out0 is not None else None
+    return s / (t_dft + t_pts), orc.num_threads(), s, err
+
+
+def run_reference(a, world, rank):
+    """The reference arm: the CPU oracle as it stands, timed per step on a bounded
+    sample (the input's DFT plus direct sums at 64 random outputs)."""
+    if rank != 0:
+        return
+    from oracle import oracle as orc
+    from paper_math_0610051_gb300 import synth
+    ph = orc.Phase(orc.ELLIPSE, synth.ellipse_params())
+    amp = orc.Amplitude()
+    s = 64
+    times = []
+    for k in range(a.warmup + a.steps):
+        f = synth.white_noise(a.N, 1, seed=k)[0]
+        n1, n2 = synth.sample_points(a.N, s, seed=1000 + k)
+        t0 = time.perf_counter()
+        orc.apply_points(ph, amp, orc.dft2(f), n1, n2)
+        if k >= a.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = s * a.steps / total
+    cores = orc.num_threads()
+    sample = f"per step: unitary DFT of one {a.N}x{a.N} input + direct sums (Eq. dfio) at {s} random x"
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": a.gpus,
+        "steps": a.steps, "warmup": a.warmup, "ms_per_step": 1e3 * total / a.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(a), "N": a.N, "eps": a.eps,
+                   "oracle_sample_points_per_step": s},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------- our arm -----
+
+def run_ours(a, world, rank, local):
+    import numpy as np
+    import torch
+    import __graft_entry__
+    __graft_entry__.build_library()
+    from paper_math_0610051_gb300 import fio, synth
+
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    N, B = a.N, a.batch
+    prm = synth.ellipse_params()
+    t0 = time.perf_counter()
+    plan = fio.Plan(N, fio.PHASE_ELLIPSE, prm, a.eps, max_batch=B)
+    plan_s = time.perf_counter() - t0
+    info = plan.info()
+    log(f"[rank {rank}] plan: {plan_s:.1f}s L={info['L']} q mean {info['q_mean']:.2f} "
+        f"max {info['q_max']} sep err {info['sep_error']:.2e} "
+        f"bytes {info['bytes_total'] / 1e9:.2f} GB")
+    f_np = synth.white_noise(N, B, seed=10 + rank)
+    g_np = synth.white_noise(N, B, seed=5000 + rank, real=False)
+    f = torch.from_numpy(f_np).to(torch.complex64).to(dev)
+    g = torch.from_numpy(g_np).to(torch.complex64).to(dev)
+    lf = torch.empty_like(f)
+    lsg = torch.empty_like(g)
+
+    def step():
+        plan.apply(f, lf)
+        plan.adjoint(g, lsg)
+
+    for _ in range(a.warmup):
+        step()
+    torch.cuda.synchronize()
+    barrier()
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    sampler = ClockSampler(vis.split(",")[local] if vis else str(local))
+    sampler.start()
+    time.sleep(0.3)
+    plan.set_timing(True)
+    plan.stage_times()
+    l0 = plan.info()["kernel_launches"]
+    stream = torch.cuda.current_stream(dev)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(a.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    ms = e0.elapsed_time(e1)
+    stages = plan.stage_times()
+    plan.set_timing(False)
+    launches = plan.info()["kernel_launches"] - l0
+    clocks = sampler.stop()
+    ms_max = allreduce(ms, "max")
+    launches_all = int(allreduce(launches, "sum"))
+    outputs = 2 * B * N * N * a.steps * world
+    value = outputs / (ms_max / 1e3)
+
+    # roofline of the dominant stage (largest share of event time)
+    sb = stage_bytes(plan, B)
+    top = max(stages, key=lambda k: stages[k][0])
+    top_ms, top_cnt = stages[top]
+    per_launch_s = top_ms / max(top_cnt, 1) / 1e3
+    achieved = sb[top] / per_launch_s / 1e9
+    peak, peak_kind = peaks()
+    kname = {"S3_interp": "k_interp", "S4a_spread": "k_spread"}.get(top, top)
+    roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                "frac": achieved / peak, "traffic": recorded_traffic(kname, B, N),
+                "kernel": top, "peak_source": peak_kind,
+                "alg_bytes_per_launch": sb[top], "launch_ms": per_launch_s * 1e3}
+    fwd_ms = sum(stages[s][0] for s in ("S0_dft", "S1_scatter", "S2_colfft", "S3_interp"))
+    adj_ms = sum(stages[s][0] for s in stages) - fwd_ms
+    stage_line = {s: {"ms_per_launch": stages[s][0] / max(stages[s][1], 1),
+                      "share": stages[s][0] / max(sum(v[0] for v in stages.values()), 1e-9),
+                      "GB_per_s": sb[s] / (stages[s][0] / max(stages[s][1], 1) / 1e3) / 1e9}
+                  for s in stages}
+
+    # end to end through the public API with pinned host buffers
+    fh_ = torch.from_numpy(f_np).to(torch.complex64).pin_memory()
+    gh_ = torch.from_numpy(g_np).to(torch.complex64).pin_memory()
+    lfh = torch.empty_like(fh_).pin_memory()
+    lsgh = torch.empty_like(gh_).pin_memory()
+    ke = max(3, a.steps // 2)
+
+    def e2e_step():
+        f.copy_(fh_, non_blocking=True)
+        g.copy_(gh_, non_blocking=True)
+        plan.apply(f, lf)
+        plan.adjoint(g, lsg)
+        lfh.copy_(lf, non_blocking=True)
+        lsgh.copy_(lsg, non_blocking=True)
+
+    e2e_step()
+    torch.cuda.synchronize()
+    barrier()
+    e0.record(stream)
+    for _ in range(ke):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    e2e_ms = allreduce(e0.elapsed_time(e1), "max")
+    e2e = {"value": 2 * B * N * N * ke * world / (e2e_ms / 1e3), "unit": UNIT,
+           "h2d_bytes_per_step": 2 * B * N * N * 8, "d2h_bytes_per_step": 2 * B * N * N * 8}
+
+    extra = {}
+    out0 = lf[0].cpu().numpy().astype(np.complex128)
+    if rank == 0 and world == 1 and not a.no_fp64:
+        # the FP64 path at the same eps: accuracy reference and speed comparison
+        p64 = fio.Plan(N, fio.PHASE_ELLIPSE, prm, a.eps, precision="fp64", max_batch=1)
+        f64 = f[:1].to(torch.complex128)
+        g64 = g[:1].to(torch.complex128)
+        o64 = p64.apply(f64)
+        rel = float(torch.linalg.vector_norm(o64 - lf[:1].to(torch.complex128)) /
+                    torch.linalg.vector_norm(o64))
+        for _ in range(2):
+            p64.apply(f64)
+            p64.adjoint(g64)
+        torch.cuda.synchronize()
+        e0.record(stream)
+        k64 = 5
+        for _ in range(k64):
+            p64.apply(f64)
+            p64.adjoint(g64)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = e0.elapsed_time(e1)
+        extra["rel_l2_mixed_vs_fp64"] = rel
+        extra["fp64_path"] = {"outputs_per_s": 2 * N * N * k64 / (ms64 / 1e3), "batch": 1,
+                              "ms_per_step": ms64 / k64}
+        p64.close()
+    if rank == 0 and world == 1 and not a.no_cpu:
+        rate, cores, s, err = cpu_oracle_rate(N, f_np[0], out0=out0)
+        extra["cpu_baseline"] = {
+            "value": rate, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": f"forward direct sums (Eq. dfio, FP64) at {s} random x of input 0, "
+                      f"its {N}x{N} DFT included"}
+        extra["rel_l2_vs_oracle"] = err
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": ms_max / a.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "c64", "data": "synthetic",
+        "config": {"workload": workload_name(a), "N": N, "batch": B, "eps": a.eps,
+                   "precision": "mixed (complex64 apply, FP64 plan)", "L": info["L"],
+                   "q_mean": info["q_mean"], "q_max": info["q_max"],
+                   "sep_error": info["sep_error"], "kb_width": info["kb_width"],
+                   "outputs_per_step": 2 * B * N * N,
+                   "l2": "no flush: each step streams alpha (%.1f GB) and the grids, far above the 129 MB L2"
+                         % (info["bytes_alpha"] / 1e9),
+                   "parallelism": f"replicas x{world}", "plan_seconds": plan_s},
+        "roofline": roofline,
+        "e2e": e2e,
+        "gpu_launches": launches_all,
+        "clocks": clocks,
+        "per_direction": {"forward_outputs_per_s": B * N * N * a.steps / (fwd_ms / 1e3),
+                          "adjoint_outputs_per_s": B * N * N * a.steps / (adj_ms / 1e3)},
+        "stages": stage_line,
+    }
+    line.update(extra)
+    print(json.dumps(line), flush=True)
+    plan.close()
+
+
+def main():
+    a = parse()
+    world, rank, local = dist_setup()
+    if a.impl == "reference":
+        run_reference(a, world, rank)
+    else:
+        run_ours(a, world, rank, local)
+
+
+if __name__ == "__main__":
+    main()

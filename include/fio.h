@@ -143,6 +143,7 @@ typedef struct {
   unsigned long long grid_points;   /* sum over wedges of m1*m2*q (one input) */
   unsigned long long alg_bytes_apply; /* algorithmic HBM bytes of one batch-1 apply */
   double plan_seconds;              /* wall time of fio_plan_create */
+  unsigned long long kernel_launches; /* this plan's kernel launches so far (all applies) */
   double sep_error;                 /* largest per-wedge estimate of the relative Frobenius
                                        error of the separated factors (Sec. 4, Table 1's
                                        estimator over every column, on 200 random rows) */
@@ -160,6 +161,30 @@ typedef struct {
   int r;             /* final random sample count */
   int npts;          /* |W_l|: frequencies owned by this wedge */
 } fio_wedge_info;
+
+/* Stages of the apply path, for per-stage timing (Sec. 3.4 and 3.5 steps). */
+typedef enum {
+  FIO_STAGE_S0_DFT = 0,      /* unitary 2D DFT of the input */
+  FIO_STAGE_S1_SCATTER = 1,  /* beta' fhat placed in the grids, row FFTs */
+  FIO_STAGE_S2_COLFFT = 2,   /* column FFTs of the grids */
+  FIO_STAGE_S3_INTERP = 3,   /* KB interpolation, alpha' multiply, sums over t and l */
+  FIO_STAGE_S4A_SPREAD = 4,  /* adjoint: type-1 spread of conj(alpha') g */
+  FIO_STAGE_S4B_COLFFT = 5,  /* adjoint: column FFTs, box rows kept */
+  FIO_STAGE_S4B_ROWFFT = 6,  /* adjoint: row FFTs, wedge runs kept */
+  FIO_STAGE_S4C_GATHER = 7,  /* adjoint: sum_t conj(beta') Ghat into the owner wedge */
+  FIO_STAGE_S4D_IDFT = 8,    /* adjoint: inverse unitary 2D DFT */
+  FIO_NUM_STAGES = 9
+} fio_stage;
+
+/* Turn per-stage timing on or off.  When on, every apply records a pair of CUDA
+ * events around each stage on the launch stream (a few microseconds each). */
+fio_status fio_plan_set_timing(fio_plan plan, int on);
+
+/* Stage times accumulated since the previous call: ms[s] = summed event time of
+ * stage s in milliseconds, count[s] = its number of timed executions (host
+ * arrays of FIO_NUM_STAGES; either may be NULL).  Synchronises on the recorded
+ * events, then resets the accumulators. */
+fio_status fio_plan_stage_times(fio_plan plan, double *ms, long long *count);
 
 /* Geometry and rank of wedge l (0 <= l < L). */
 fio_status fio_plan_get_wedge(fio_plan plan, int l, fio_wedge_info *info);

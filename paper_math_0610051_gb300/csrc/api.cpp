@@ -99,6 +99,7 @@ fio_status fio_plan_create(int N, const fio_phase *phase, const fio_amplitude *a
 
 void fio_plan_destroy(fio_plan p) {
   if (!p) return;
+  release_timing_events(p);
   free_plan_device(p);
   delete p;
 }
@@ -155,6 +156,33 @@ fio_status fio_plan_get_info(fio_plan p, fio_plan_info *info) {
   info->alg_bytes_apply = p->alg_bytes;
   info->plan_seconds = p->plan_seconds;
   info->sep_error = p->sep_err;
+  info->kernel_launches = p->launches;
+  return FIO_OK;
+}
+
+fio_status fio_plan_set_timing(fio_plan p, int on) {
+  if (!plan_ok(p)) return FIO_EINVAL;
+  p->timing = on != 0;
+  return FIO_OK;
+}
+
+fio_status fio_plan_stage_times(fio_plan p, double *ms, long long *count) {
+  if (!plan_ok(p)) return FIO_EINVAL;
+  if (ms)
+    for (int i = 0; i < FIO_NUM_STAGES; ++i) ms[i] = 0.0;
+  if (count)
+    for (int i = 0; i < FIO_NUM_STAGES; ++i) count[i] = 0;
+  for (size_t k = 0; k < p->ev_used; ++k) {
+    cudaError_t e = cudaEventSynchronize(p->ev_pool[2 * k + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "fio_plan_stage_times");
+    float t = 0.f;
+    e = cudaEventElapsedTime(&t, p->ev_pool[2 * k], p->ev_pool[2 * k + 1]);
+    if (e != cudaSuccess) return cuda_fail(e, "fio_plan_stage_times");
+    const int st = p->ev_stage[k];
+    if (ms) ms[st] += t;
+    if (count) count[st] += 1;
+  }
+  p->ev_used = 0;
   return FIO_OK;
 }
 

@@ -471,6 +471,38 @@ static LaunchGeom geom(const fio_plan_s *p, int B, int nl_col) {
   return g;
 }
 
+// Per-stage timing: a (start, stop) event pair recorded around a stage on the
+// launch stream when the plan's timing flag is set.
+struct StageTimer {
+  const fio_plan_s *p;
+  cudaStream_t s;
+  size_t pair = (size_t)-1;
+  StageTimer(const fio_plan_s *plan, cudaStream_t st, int stage) : p(plan), s(st) {
+    if (!p->timing) return;
+    if (2 * (p->ev_used + 1) > p->ev_pool.size()) {
+      cudaEvent_t a, b;
+      if (cudaEventCreate(&a) != cudaSuccess) return;
+      if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return; }
+      p->ev_pool.push_back(a);
+      p->ev_pool.push_back(b);
+    }
+    pair = p->ev_used++;
+    if (p->ev_stage.size() < p->ev_used) p->ev_stage.resize(p->ev_used);
+    p->ev_stage[pair] = stage;
+    cudaEventRecord(p->ev_pool[2 * pair], s);
+  }
+  ~StageTimer() {
+    if (pair != (size_t)-1) cudaEventRecord(p->ev_pool[2 * pair + 1], s);
+  }
+};
+
+void release_timing_events(fio_plan_s *p) {
+  for (cudaEvent_t e : p->ev_pool) cudaEventDestroy(e);
+  p->ev_pool.clear();
+  p->ev_stage.clear();
+  p->ev_used = 0;
+}
+
 static FftPlanDev plan_for_N(const fio_plan_s *p, const void **tw) {
   for (const auto &f : p->ffts)
     if (f.n == p->N) {
@@ -492,7 +524,11 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
   const FftPlanDev plN = plan_for_N(p, &twN);
   cudaError_t e;
   // S0: fhat in natural order (no centring shift)
-  e = dft2_impl<T>(N, f, p->d_fhat, B, 0, plN, twN, false, s);
+  {
+    StageTimer st(p, s, FIO_STAGE_S0_DFT);
+    e = dft2_impl<T>(N, f, p->d_fhat, B, 0, plN, twN, false, s);
+    p->launches += 2;
+  }
   if (e != cudaSuccess) return e;
   const LaunchGeom g0 = geom(p, B, 1);
   // S1
@@ -500,20 +536,32 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
   const size_t sm1 = apply_smem_bytes(g0.max_m2, nl1, prec);
   if ((e = set_smem(k_scatter_rowfft<T>, sm1)) != cudaSuccess) return e;
   dim3 g1((unsigned)p->rows.size(), (unsigned)((B * g0.max_q + nl1 - 1) / nl1));
-  k_scatter_rowfft<T><<<g1, kThreads, sm1, s>>>((const C *)p->d_fhat, p->d_wedges, p->d_rows,
-                                                p->d_ffts, (const C *)p->d_twiddle,
-                                                (const C *)p->d_beta, (C *)p->d_grid, N, B, nl1);
+  {
+    StageTimer st(p, s, FIO_STAGE_S1_SCATTER);
+    k_scatter_rowfft<T><<<g1, kThreads, sm1, s>>>((const C *)p->d_fhat, p->d_wedges, p->d_rows,
+                                                  p->d_ffts, (const C *)p->d_twiddle,
+                                                  (const C *)p->d_beta, (C *)p->d_grid, N, B, nl1);
+    p->launches += 1;
+  }
   // S2
   const int nl2 = pick_nl(g0.max_m1, prec, 16);
   const size_t sm2 = apply_smem_bytes(g0.max_m1, nl2, prec);
   if ((e = set_smem(k_colfft<T>, sm2)) != cudaSuccess) return e;
   const LaunchGeom g2 = geom(p, B, nl2);
-  k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)p->d_grid, p->d_wedges, p->d_ffts,
-                                                   (const C *)p->d_twiddle, L, B, nl2, 0);
+  {
+    StageTimer st(p, s, FIO_STAGE_S2_COLFFT);
+    k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)p->d_grid, p->d_wedges, p->d_ffts,
+                                                     (const C *)p->d_twiddle, L, B, nl2, 0);
+    p->launches += 1;
+  }
   // S3
   dim3 g3((unsigned)((NN + kThreads - 1) / kThreads), (unsigned)B);
-  k_interp<T><<<g3, kThreads, 0, s>>>((const C *)p->d_grid, p->d_wedges, (const C *)p->d_alpha,
-                                      p->d_warp, (C *)out, N, L, B, make_kb(p));
+  {
+    StageTimer st(p, s, FIO_STAGE_S3_INTERP);
+    k_interp<T><<<g3, kThreads, 0, s>>>((const C *)p->d_grid, p->d_wedges, (const C *)p->d_alpha,
+                                        p->d_warp, (C *)out, N, L, B, make_kb(p));
+    p->launches += 1;
+  }
   return cudaGetLastError();
 }
 
@@ -530,29 +578,47 @@ static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out,
   e = cudaMemsetAsync(p->d_grid, 0, (size_t)p->grid_units * B * cs, s);
   if (e != cudaSuccess) return e;
   dim3 ga((unsigned)((NN + kThreads - 1) / kThreads), (unsigned)B);
-  k_spread<T><<<ga, kThreads, 0, s>>>((const C *)gin, (C *)p->d_grid, p->d_wedges,
-                                      (const C *)p->d_alpha, p->d_warp, N, L, B, make_kb(p));
+  {
+    StageTimer st(p, s, FIO_STAGE_S4A_SPREAD);
+    k_spread<T><<<ga, kThreads, 0, s>>>((const C *)gin, (C *)p->d_grid, p->d_wedges,
+                                        (const C *)p->d_alpha, p->d_warp, N, L, B, make_kb(p));
+    p->launches += 1;
+  }
   // S4b columns
   const LaunchGeom g0 = geom(p, B, 1);
   const int nl2 = pick_nl(g0.max_m1, prec, 16);
   const size_t sm2 = apply_smem_bytes(g0.max_m1, nl2, prec);
   if ((e = set_smem(k_colfft<T>, sm2)) != cudaSuccess) return e;
   const LaunchGeom g2 = geom(p, B, nl2);
-  k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)p->d_grid, p->d_wedges, p->d_ffts,
-                                                   (const C *)p->d_twiddle, L, B, nl2, 1);
+  {
+    StageTimer st(p, s, FIO_STAGE_S4B_COLFFT);
+    k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)p->d_grid, p->d_wedges, p->d_ffts,
+                                                     (const C *)p->d_twiddle, L, B, nl2, 1);
+    p->launches += 1;
+  }
   // S4b rows
   const int nl1 = pick_nl(g0.max_m2, prec, 16);
   const size_t sm1 = apply_smem_bytes(g0.max_m2, nl1, prec);
   if ((e = set_smem(k_rowfft_adj<T>, sm1)) != cudaSuccess) return e;
   dim3 g1((unsigned)p->rows.size(), (unsigned)((B * g0.max_q + nl1 - 1) / nl1));
-  k_rowfft_adj<T><<<g1, kThreads, sm1, s>>>((C *)p->d_grid, p->d_wedges, p->d_rows, p->d_ffts,
-                                            (const C *)p->d_twiddle, B, nl1);
+  {
+    StageTimer st(p, s, FIO_STAGE_S4B_ROWFFT);
+    k_rowfft_adj<T><<<g1, kThreads, sm1, s>>>((C *)p->d_grid, p->d_wedges, p->d_rows, p->d_ffts,
+                                              (const C *)p->d_twiddle, B, nl1);
+    p->launches += 1;
+  }
   // S4c
-  k_gather_adj<T><<<(unsigned)p->rows.size(), kThreads, 0, s>>>(
-      (const C *)p->d_grid, p->d_wedges, p->d_rows, (const C *)p->d_beta, (C *)p->d_fhat, N, B);
+  {
+    StageTimer st(p, s, FIO_STAGE_S4C_GATHER);
+    k_gather_adj<T><<<(unsigned)p->rows.size(), kThreads, 0, s>>>(
+        (const C *)p->d_grid, p->d_wedges, p->d_rows, (const C *)p->d_beta, (C *)p->d_fhat, N, B);
+    p->launches += 1;
+  }
   // S4d: inverse unitary DFT from natural order
   const void *twN;
   const FftPlanDev plN = plan_for_N(p, &twN);
+  StageTimer st(p, s, FIO_STAGE_S4D_IDFT);
+  p->launches += 2;
   return dft2_impl<T>(N, p->d_fhat, out, B, 1, plN, twN, false, s);
 }
 

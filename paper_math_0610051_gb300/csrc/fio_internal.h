@@ -96,6 +96,13 @@ struct fio_plan_s {
   size_t bytes_total = 0;
   unsigned long long alg_bytes = 0;
 
+  // diagnostics: launch counter and optional per-stage CUDA-event timing
+  mutable unsigned long long launches = 0;
+  bool timing = false;
+  mutable std::vector<cudaEvent_t> ev_pool;   // pairs (start, stop)
+  mutable std::vector<int> ev_stage;          // stage of each used pair
+  mutable size_t ev_used = 0;
+
 };
 
 namespace fio {
@@ -120,6 +127,7 @@ cudaError_t launch_adjoint(const fio_plan_s *p, const void *g, void *out, int ba
 cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int batch, int inverse,
                         const FftPlanDev *d_plan, const void *d_tw, cudaStream_t s);
 size_t apply_smem_bytes(int n, int nl, int precision);
+void release_timing_events(fio_plan_s *p);
 
 // plan_kernels.cu (FP64 plan construction on the device)
 struct PhaseDev {

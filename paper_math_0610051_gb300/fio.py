@@ -52,7 +52,7 @@ class _PlanInfo(ctypes.Structure):
                 ("bytes_warp", ctypes.c_ulonglong), ("bytes_grid", ctypes.c_ulonglong),
                 ("bytes_total", ctypes.c_ulonglong), ("grid_points", ctypes.c_ulonglong),
                 ("alg_bytes_apply", ctypes.c_ulonglong), ("plan_seconds", ctypes.c_double),
-                ("sep_error", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_ulonglong), ("sep_error", ctypes.c_double)]
 
 
 class _WedgeInfo(ctypes.Structure):
@@ -66,7 +66,7 @@ class _WedgeInfo(ctypes.Structure):
 EXPORTS = [
     "fio_options_default", "fio_plan_create", "fio_apply", "fio_apply_adjoint", "fio_plan_sync",
     "fio_plan_get_info", "fio_plan_get_wedge", "fio_plan_export_wedge", "fio_plan_export_warp",
-    "fio_plan_destroy",
+    "fio_plan_destroy", "fio_plan_set_timing", "fio_plan_stage_times",
     "fio_dft2", "fio_default_wedges", "fio_wedge_map", "fio_wedge_geometry", "fio_kb_eval",
     "fio_kb_width_for", "fio_host_eigh", "fio_status_string", "fio_last_error", "fio_version",
 ]
@@ -94,6 +94,8 @@ def lib():
             L.fio_plan_get_wedge.argtypes = [P, I, ctypes.POINTER(_WedgeInfo)]
             L.fio_plan_export_wedge.argtypes = [P, I, P, P, P, P]
             L.fio_plan_export_warp.argtypes = [P, I, P]
+            L.fio_plan_set_timing.argtypes = [P, I]
+            L.fio_plan_stage_times.argtypes = [P, P, P]
             L.fio_plan_destroy.argtypes = [P]
             L.fio_plan_destroy.restype = None
             L.fio_dft2.argtypes = [I, I, P, P, I, I, P]
@@ -216,6 +218,21 @@ class Plan:
     def sync(self):
         _check(lib().fio_plan_sync(self._handle, _stream_ptr(self._torch, self.device)),
                "fio_plan_sync")
+
+    # -- diagnostics
+    STAGES = ["S0_dft", "S1_scatter", "S2_colfft", "S3_interp", "S4a_spread", "S4b_colfft",
+              "S4b_rowfft", "S4c_gather", "S4d_idft"]
+
+    def set_timing(self, on: bool = True):
+        _check(lib().fio_plan_set_timing(self._handle, int(bool(on))), "fio_plan_set_timing")
+
+    def stage_times(self) -> dict:
+        """{stage: (total ms, executions)} since the previous call (synchronises)."""
+        ms = np.zeros(len(self.STAGES))
+        cnt = np.zeros(len(self.STAGES), np.int64)
+        _check(lib().fio_plan_stage_times(self._handle, _np_ptr(ms), _np_ptr(cnt)),
+               "fio_plan_stage_times")
+        return {s: (float(ms[i]), int(cnt[i])) for i, s in enumerate(self.STAGES)}
 
     # -- introspection
     def info(self) -> dict:
