@@ -144,6 +144,8 @@ typedef struct {
   unsigned long long alg_bytes_apply; /* algorithmic HBM bytes of one batch-1 apply */
   double plan_seconds;              /* wall time of fio_plan_create */
   unsigned long long kernel_launches; /* this plan's kernel launches so far (all applies) */
+  int max_footprint;                /* largest grid footprint (cells) of a 16 x 16 point tile */
+  double mean_footprint;            /* mean footprint over (wedge, tile) */
   double sep_error;                 /* largest per-wedge estimate of the relative Frobenius
                                        error of the separated factors (Sec. 4, Table 1's
                                        estimator over every column, on 200 random rows) */

@@ -15,61 +15,18 @@
 // FFTs (exp(-2 pi i)) with pruned output, S4c sum_t conj(beta') G into the
 // owner wedge's frequencies, S4d inverse unitary DFT.
 //
-// Grid layout: wedge l's grid is [g1 < m1][g2 < m2][ch < B q_l], ch = b q_l + t.
+// Grid layout: wedge l's grid is [g1 < m1][g2 < m2][ch < B qp_l], ch = b qp_l + t
+// (qp_l = q_l rounded up to even; the padded term has zero factors).
 #include <cuda_runtime.h>
 
 #include <algorithm>
 #include <cstdint>
 
+#include "apply_common.cuh"
 #include "fft_engine.cuh"
 #include "fio_internal.h"
 
 namespace fio {
-
-template <typename T> using Cx = typename CxT<T>::type;
-
-__device__ __forceinline__ int imodp(int a, int n) {
-  int r = a % n;
-  return r < 0 ? r + n : r;
-}
-
-constexpr int kThreads = 256;
-
-// ------------------------------------------------------------ KB kernel ----
-// phi(s) = I0(beta sqrt(1 - (2s/w)^2)) / I0(beta) for |s| < w/2, else 0.
-__device__ __forceinline__ float kb_phi(float s, float two_over_w, float beta, float inv_i0b) {
-  float z = s * two_over_w;
-  float a = 1.0f - z * z;
-  return a > 0.0f ? cyl_bessel_i0f(beta * sqrtf(a)) * inv_i0b : 0.0f;
-}
-__device__ __forceinline__ double kb_phi(double s, double two_over_w, double beta,
-                                         double inv_i0b) {
-  double z = s * two_over_w;
-  double a = 1.0 - z * z;
-  return a > 0.0 ? cyl_bessel_i0(beta * sqrt(a)) * inv_i0b : 0.0;
-}
-
-struct KbDev {
-  int w;
-  double beta, inv_i0b;
-};
-
-// Decode a 32-bit fraction y' (of one axis) into the first grid cell of the
-// width-w window and the w weights: u = y' m, cells j0..j0+w-1 (mod m),
-// weight phi(u - j).
-template <typename T>
-__device__ __forceinline__ int kb_window(uint32_t Y, int m, const KbDev &kb, T *wgt) {
-  const unsigned long long P = (unsigned long long)Y * (unsigned)m;
-  const int i = (int)(P >> 32);
-  const T f = (T)(uint32_t)P * T(2.3283064365386962890625e-10);  // 2^-32
-  const int hw = kb.w >> 1;
-  int j0 = i - hw + 1;
-  if (kb.w & 1) j0 = i - hw + (f >= T(0.5) ? 1 : 0);
-  const T base = f + T(i - j0);
-  const T tw = T(2.0) / T(kb.w), beta = T(kb.beta), inv = T(kb.inv_i0b);
-  for (int a = 0; a < kb.w; ++a) wgt[a] = kb_phi(base - T(a), tw, beta, inv);
-  return imodp(j0, m);
-}
 
 // --------------------------------------------------------------- S0 / S4d --
 // Unitary 2D DFT passes.  Rows: lines are rows of N contiguous elements.
@@ -157,7 +114,7 @@ k_scatter_rowfft(const Cx<T> *__restrict__ fhat, const WedgeDev *__restrict__ W,
   extern __shared__ unsigned char smem_raw[];
   const RowDev rw = rows[blockIdx.x];
   const WedgeDev w = W[rw.wedge];
-  const int nch = B * w.q;
+  const int nch = B * w.qp;
   const int c0 = blockIdx.y * nl;
   if (c0 >= nch) return;
   const int nlc = min(nl, nch - c0);
@@ -171,7 +128,7 @@ k_scatter_rowfft(const Cx<T> *__restrict__ fhat, const WedgeDev *__restrict__ W,
   const int k1pp = rw.xi1 + w.xc1;
   for (int it = threadIdx.x; it < rw.len * nlc; it += blockDim.x) {
     const int l = it % nlc, j = it / nlc;
-    const int ch = c0 + l, bb = ch / w.q, t = ch - bb * w.q;
+    const int ch = c0 + l, bb = ch / w.qp, t = ch - bb * w.qp;
     const int x2p = rw.a + j;
     const int k2pp = x2p + w.xc2;
     const int k1 = w.Minv[0] * k1pp + w.Minv[1] * k2pp;
@@ -205,13 +162,13 @@ k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   // locate (wedge, chunk) for this block
   int blk = blockIdx.x, l = 0;
   for (; l < L; ++l) {
-    const int cnt = (W[l].m2 * B * W[l].q + nl - 1) / nl;
+    const int cnt = (W[l].m2 * B * W[l].qp + nl - 1) / nl;
     if (blk < cnt) break;
     blk -= cnt;
   }
   if (l >= L) return;
   const WedgeDev w = W[l];
-  const int nch = B * w.q;
+  const int nch = B * w.qp;
   const long long rs = (long long)w.m2 * nch;  // row stride
   const long long cc0 = (long long)blk * nl;
   const int nlc = (int)min((long long)nl, rs - cc0);
@@ -251,91 +208,6 @@ k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   }
 }
 
-// ----------------------------------------------------------------- S3 ------
-// One thread per (x, b): sum over wedges l and terms t of
-// alpha'_t(x) * sum_{cells} phi phi G_{l t}.
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_interp(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
-         const Cx<T> *__restrict__ alpha, const uint2 *__restrict__ warp, Cx<T> *__restrict__ out,
-         int N, int L, int B, KbDev kb) {
-  using C = Cx<T>;
-  const long long NN = (long long)N * N;
-  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int bb = blockIdx.y;
-  if (x >= NN) return;
-  T w1[kMaxKbWidth], w2[kMaxKbWidth];
-  C acc{0, 0};
-  for (int l = 0; l < L; ++l) {
-    const WedgeDev &w = W[l];
-    const uint2 Y = warp[l * NN + x];
-    const int j1 = kb_window<T>(Y.x, w.m1, kb, w1);
-    const int j2 = kb_window<T>(Y.y, w.m2, kb, w2);
-    const int nch = B * w.q;
-    const C *g = grid + w.grid_unit * B + bb * w.q;
-    for (int t = 0; t < w.q; ++t) {
-      C v{0, 0};
-      int c1 = j1;
-      for (int a1 = 0; a1 < kb.w; ++a1) {
-        C r{0, 0};
-        int c2 = j2;
-        const C *grow = g + (long long)c1 * w.m2 * nch + t;
-        for (int a2 = 0; a2 < kb.w; ++a2) {
-          const C gv = grow[(long long)c2 * nch];
-          r.x += w2[a2] * gv.x;
-          r.y += w2[a2] * gv.y;
-          if (++c2 == w.m2) c2 = 0;
-        }
-        v.x += w1[a1] * r.x;
-        v.y += w1[a1] * r.y;
-        if (++c1 == w.m1) c1 = 0;
-      }
-      const C al = alpha[w.alpha_off + t * NN + x];
-      acc = cadd(acc, cmul(al, v));
-    }
-  }
-  out[bb * NN + x] = acc;
-}
-
-// ----------------------------------------------------------------- S4a -----
-// Type-1 spread: G_{l t} += phi phi conj(alpha'_t(x)) g(x).
-template <typename T>
-__global__ void __launch_bounds__(kThreads)
-k_spread(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
-         const Cx<T> *__restrict__ alpha, const uint2 *__restrict__ warp, int N, int L, int B,
-         KbDev kb) {
-  using C = Cx<T>;
-  const long long NN = (long long)N * N;
-  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const int bb = blockIdx.y;
-  if (x >= NN) return;
-  T w1[kMaxKbWidth], w2[kMaxKbWidth];
-  const C gv = gin[bb * NN + x];
-  for (int l = 0; l < L; ++l) {
-    const WedgeDev &w = W[l];
-    const uint2 Y = warp[l * NN + x];
-    const int j1 = kb_window<T>(Y.x, w.m1, kb, w1);
-    const int j2 = kb_window<T>(Y.y, w.m2, kb, w2);
-    const int nch = B * w.q;
-    C *g = grid + w.grid_unit * B + bb * w.q;
-    for (int t = 0; t < w.q; ++t) {
-      const C c = cmulc(gv, alpha[w.alpha_off + t * NN + x]);  // g * conj(alpha)
-      int c1 = j1;
-      for (int a1 = 0; a1 < kb.w; ++a1) {
-        int c2 = j2;
-        T* grow = reinterpret_cast<T *>(g + (long long)c1 * w.m2 * nch + t);
-        for (int a2 = 0; a2 < kb.w; ++a2) {
-          const T wt = w1[a1] * w2[a2];
-          atomicAdd(grow + 2 * (long long)c2 * nch, wt * c.x);
-          atomicAdd(grow + 2 * (long long)c2 * nch + 1, wt * c.y);
-          if (++c2 == w.m2) c2 = 0;
-        }
-        if (++c1 == w.m1) c1 = 0;
-      }
-    }
-  }
-}
-
 // ---------------------------------------------------------------- S4b rows --
 // Row FFT along g2 with exp(-2 pi i) for each box row; only the run's
 // columns are written back.
@@ -348,7 +220,7 @@ k_rowfft_adj(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   extern __shared__ unsigned char smem_raw[];
   const RowDev rw = rows[blockIdx.x];
   const WedgeDev w = W[rw.wedge];
-  const int nch = B * w.q;
+  const int nch = B * w.qp;
   const int c0 = blockIdx.y * nl;
   if (c0 >= nch || rw.len == 0) return;
   const int nlc = min(nl, nch - c0);
@@ -381,15 +253,15 @@ k_gather_adj(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   using C = Cx<T>;
   const RowDev rw = rows[blockIdx.x];
   const WedgeDev w = W[rw.wedge];
-  const int nch = B * w.q;
+  const int nch = B * w.qp;
   const C *row = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * w.m2 * nch;
   const int k1pp = rw.xi1 + w.xc1;
   for (int it = threadIdx.x; it < rw.len * B; it += blockDim.x) {
     const int j = it % rw.len, bb = it / rw.len;
     const int x2p = rw.a + j;
-    const C *cell = row + (long long)imodp(x2p, w.m2) * nch + bb * w.q;
+    const C *cell = row + (long long)imodp(x2p, w.m2) * nch + bb * w.qp;
     C acc{0, 0};
-    for (int t = 0; t < w.q; ++t)
+    for (int t = 0; t < w.qp; ++t)
       acc = cadd(acc, cmulc(cell[t], beta[w.beta_off + (long long)t * w.npts + rw.pt + j]));
     const int k2pp = x2p + w.xc2;
     const int k1 = w.Minv[0] * k1pp + w.Minv[1] * k2pp;
@@ -448,13 +320,6 @@ cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int bat
   return dft2_impl<float>(N, in, out, batch, inverse, *plan, d_tw, true, s);
 }
 
-static KbDev make_kb(const fio_plan_s *p) {
-  KbDev kb;
-  kb.w = p->kb.w;
-  kb.beta = p->kb.beta;
-  kb.inv_i0b = 1.0 / std::cyl_bessel_i(0.0, p->kb.beta);
-  return kb;
-}
 
 struct LaunchGeom {
   int max_m1 = 0, max_m2 = 0, max_q = 0, col_blocks = 0;
@@ -465,8 +330,8 @@ static LaunchGeom geom(const fio_plan_s *p, int B, int nl_col) {
   for (const auto &w : p->wedges) {
     g.max_m1 = std::max(g.max_m1, w.m1);
     g.max_m2 = std::max(g.max_m2, w.m2);
-    g.max_q = std::max(g.max_q, w.q);
-    g.col_blocks += (w.m2 * B * w.q + nl_col - 1) / nl_col;
+    g.max_q = std::max(g.max_q, w.qp);
+    g.col_blocks += (w.m2 * B * w.qp + nl_col - 1) / nl_col;
   }
   return g;
 }
@@ -555,11 +420,10 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
     p->launches += 1;
   }
   // S3
-  dim3 g3((unsigned)((NN + kThreads - 1) / kThreads), (unsigned)B);
   {
     StageTimer st(p, s, FIO_STAGE_S3_INTERP);
-    k_interp<T><<<g3, kThreads, 0, s>>>((const C *)p->d_grid, p->d_wedges, (const C *)p->d_alpha,
-                                        p->d_warp, (C *)out, N, L, B, make_kb(p));
+    e = launch_interp(p, p->d_grid, out, B, s);
+    if (e != cudaSuccess) return e;
     p->launches += 1;
   }
   return cudaGetLastError();
@@ -577,11 +441,10 @@ static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out,
   // S4a
   e = cudaMemsetAsync(p->d_grid, 0, (size_t)p->grid_units * B * cs, s);
   if (e != cudaSuccess) return e;
-  dim3 ga((unsigned)((NN + kThreads - 1) / kThreads), (unsigned)B);
   {
     StageTimer st(p, s, FIO_STAGE_S4A_SPREAD);
-    k_spread<T><<<ga, kThreads, 0, s>>>((const C *)gin, (C *)p->d_grid, p->d_wedges,
-                                        (const C *)p->d_alpha, p->d_warp, N, L, B, make_kb(p));
+    e = launch_spread(p, gin, p->d_grid, B, s);
+    if (e != cudaSuccess) return e;
     p->launches += 1;
   }
   // S4b columns

@@ -13,7 +13,8 @@ namespace fio {
 
 constexpr int kMaxRadixStages = 16;
 constexpr int kMaxFftLen = 4096;
-constexpr int kMaxKbWidth = 16;
+constexpr int kMaxKbWidth = 12;
+constexpr int kMaxHornerDeg = 15;
 
 // One FFT length: its radix factorisation (Stockham stages) and where its
 // twiddle table exp(-2 pi i k / n), k < n, starts in the plan's table.
@@ -33,14 +34,22 @@ struct WedgeDev {
   int b2, n2;     // columns xi'_2 in [b2, b2 + n2)
   int m1, m2;     // oversampled grid dims
   int q;          // separation rank
+  int qp;         // q rounded up to even: rank terms stored per input (the padded term is zero)
   int npts;       // |W_l|
   int fft1, fft2;         // FftPlanDev index for lengths m1, m2
   int row_off;            // first RowDev of this wedge
-  long long grid_unit;    // grid offset in units of complex * batch: sum_{l'<l} m1 m2 q
+  long long grid_unit;    // grid offset in units of complex * batch: sum_{l'<l} m1 m2 qp
   long long alpha_off;    // complex offset of alpha[l][0][0] (layout [t][x])
   long long beta_off;     // complex offset of beta[l][0][0]  (layout [t][p])
   int pt_off;             // first point of this wedge in the global point order
   int tw1_off, tw2_off;   // twiddle offsets for m1 / m2 (copies of the FftPlanDev fields)
+};
+
+// Piecewise-polynomial KB weights for the FP32 path: with z = u - j0 - (w/2 - 1)
+// in [0, 1) and t = 2z - 1, phi(u - j0 - a) = sum_k c[k][a] t^k.
+struct HornerDev {
+  int deg;
+  float c[kMaxHornerDeg + 1][kMaxKbWidth];
 };
 
 // One box row xi'_1 = b1 + r: the wedge's frequencies on it are the contiguous
@@ -88,11 +97,19 @@ struct fio_plan_s {
   fio::RowDev *d_rows = nullptr;
   fio::FftPlanDev *d_ffts = nullptr;
   void *d_twiddle = nullptr;      // complex (float2 / double2) exp(-2 pi i k/n) tables
-  void *d_alpha = nullptr;        // gamma^x * centre phase / N, [l][t][x]
+  void *d_alpha = nullptr;        // gamma^x * centre phase / N, [l][tile][point][t]
   void *d_beta = nullptr;         // gamma^xi / phihat, [l][t][p]
   uint2 *d_warp = nullptr;        // warped points y' mod 1 as 32-bit fractions, [l][x]
+  uint2 *d_warpt = nullptr;       // the same in tile order, [l][tile][point]
+  fio::HornerDev horner{};
   void *d_grid = nullptr;         // NUFFT grids [l][g1][g2][b*q + t]
   void *d_fhat = nullptr;         // spectrum workspace, batch * N * N complex
+  int4 *d_tiles = nullptr;        // per (wedge, 16x16 point tile): grid footprint (r0, c0, F1, F2)
+  int *d_errword = nullptr;       // set by a kernel whose in-kernel bounds check fails
+  int ntile = 0;                  // tiles per grid side
+  int max_foot = 0;               // largest F1 * F2 over all (wedge, tile)
+  int foot_p99 = 0;               // 99th percentile of the padded footprint plane (16-byte units)
+  double mean_foot = 0;           // mean F1 * F2
   size_t bytes_total = 0;
   unsigned long long alg_bytes = 0;
 
@@ -127,6 +144,12 @@ cudaError_t launch_adjoint(const fio_plan_s *p, const void *g, void *out, int ba
 cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int batch, int inverse,
                         const FftPlanDev *d_plan, const void *d_tw, cudaStream_t s);
 size_t apply_smem_bytes(int n, int nl, int precision);
+// interp.cu
+constexpr int kTile = 16;  // point tiles of kTile x kTile grid points
+cudaError_t build_tiles(fio_plan_s *p);   // fills d_tiles, max_foot, d_warpt (synchronises)
+void fit_horner(fio_plan_s *p);           // host: piecewise-polynomial KB weights
+cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B, cudaStream_t s);
+cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s);
 void release_timing_events(fio_plan_s *p);
 
 // plan_kernels.cu (FP64 plan construction on the device)
@@ -150,10 +173,10 @@ cudaError_t plan_eval_cols(const PhaseDev &ph, const void *d_xdata, int N, const
 // Gram matrix G = A_C^H A_C (r x r), deterministic two-level reduction.
 cudaError_t plan_gram(const double2 *d_AC, long long rows, int r, double2 *d_partial,
                       int nparts, double2 *d_G, cudaStream_t s);
-// alpha[t][x] = (sum_c A_C[x][c] W[c][t]) * exp(2 pi i y'.xi_c) / N  (W = V S^-1, r x q)
+// alpha[tile][t][lane] = (sum_c A_C[x][c] W[c][t]) * exp(2 pi i y'.xi_c) / N  (W = V S^-1, r x q)
 cudaError_t plan_form_alpha(const double2 *d_AC, int N, int r, int q, const double2 *d_W,
                             const WedgeDev &w, const uint2 *d_warp_l, void *d_alpha_l,
-                            int precision, cudaStream_t s);
+                            int precision, int ntile, cudaStream_t s);
 // beta[t][p] = (sum_i P[t][i] A(x_i, xi_p)) * dec[p], P = U_R^+ (q x r),
 // dec[p] = 1 / (phihat(xi'_1/m1) phihat(xi'_2/m2)) (NUFFT deconvolution)
 cudaError_t plan_form_beta(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,

@@ -60,7 +60,7 @@ int kb_width_for(double eps) {
   // 1D relative NUFFT error of the sigma = 2 KB kernel is about 4.5 * 10^-w
   // (measured against direct sums); ask for eps / 10.
   int w = (int)std::ceil(std::log10(45.0 / eps));
-  return std::min(std::max(w, 2), kMaxKbWidth);
+  return std::min(std::max(w, 3), kMaxKbWidth);
 }
 
 double kb_beta_for(int w, double sigma) {
@@ -319,13 +319,60 @@ fio_status cuda_status(cudaError_t e, const char *what) {
   } while (0)
 
 void free_plan_device(fio_plan_s *p) {
-  void *ptrs[] = {p->d_wedges, p->d_rows,  p->d_ffts, p->d_twiddle, p->d_alpha,
-                  p->d_beta,   p->d_warp,  p->d_grid, p->d_fhat};
+  void *ptrs[] = {p->d_wedges, p->d_rows, p->d_ffts,  p->d_twiddle, p->d_alpha,  p->d_beta,
+                  p->d_warp,   p->d_grid, p->d_fhat, p->d_tiles,   p->d_errword, p->d_warpt};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   p->d_wedges = nullptr; p->d_rows = nullptr; p->d_ffts = nullptr; p->d_twiddle = nullptr;
   p->d_alpha = nullptr; p->d_beta = nullptr; p->d_warp = nullptr; p->d_grid = nullptr;
   p->d_fhat = nullptr;
+  p->d_tiles = nullptr;
+  p->d_errword = nullptr;
+  p->d_warpt = nullptr;
+}
+
+// Piecewise polynomials of the KB kernel on the w unit intervals of a window:
+// Chebyshev interpolation in t = 2z - 1 (degree max(8, w + 1)), then monomial
+// coefficients by solving the interpolation system in FP64.
+void fit_horner(fio_plan_s *p) {
+  const int w = p->kb.w;
+  const int D = std::min(std::max(8, w + 1), kMaxHornerDeg);
+  HornerDev h{};
+  h.deg = D;
+  const int n = D + 1;
+  std::vector<double> tk(n);
+  for (int k = 0; k < n; ++k) tk[k] = std::cos(M_PI * (k + 0.5) / n);
+  for (int a = 0; a < w; ++a) {
+    std::vector<double> A((size_t)n * n), y(n);
+    for (int k = 0; k < n; ++k) {
+      double pw = 1.0;
+      for (int c = 0; c < n; ++c) {
+        A[(size_t)k * n + c] = pw;
+        pw *= tk[k];
+      }
+      y[k] = kb_phi_host((tk[k] + 1.0) / 2.0 + w / 2.0 - 1.0 - a, w, p->kb.beta);
+    }
+    // Gaussian elimination with partial pivoting
+    for (int c = 0; c < n; ++c) {
+      int piv = c;
+      for (int r = c + 1; r < n; ++r)
+        if (std::abs(A[(size_t)r * n + c]) > std::abs(A[(size_t)piv * n + c])) piv = r;
+      for (int k = 0; k < n; ++k) std::swap(A[(size_t)c * n + k], A[(size_t)piv * n + k]);
+      std::swap(y[c], y[piv]);
+      for (int r = c + 1; r < n; ++r) {
+        const double f = A[(size_t)r * n + c] / A[(size_t)c * n + c];
+        for (int k = c; k < n; ++k) A[(size_t)r * n + k] -= f * A[(size_t)c * n + k];
+        y[r] -= f * y[c];
+      }
+    }
+    for (int c = n - 1; c >= 0; --c) {
+      double v = y[c];
+      for (int k = c + 1; k < n; ++k) v -= A[(size_t)c * n + k] * y[k];
+      y[c] = v / A[(size_t)c * n + c];
+    }
+    for (int k = 0; k < n; ++k) h.c[k][a] = (float)y[k];
+  }
+  p->horner = h;
 }
 
 template <typename T> static fio_status upload(void **dst, const std::vector<T> &v, const char *w) {
@@ -389,7 +436,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   const double sigma = opt.sigma > 0 ? opt.sigma : 2.0;
   if (L < 1 || L > 256 || sigma < 1.25 || sigma > 4.0) { set_error("L or sigma out of range"); return FIO_EINVAL; }
   const int w = opt.kb_width > 0 ? opt.kb_width : kb_width_for(eps);
-  if (w < 2 || w > kMaxKbWidth) { set_error("kb_width out of range"); return FIO_EINVAL; }
+  if (w < 3 || w > kMaxKbWidth) { set_error("kb_width must lie in [3, 12]"); return FIO_EINVAL; }
   const int r0 = opt.r0 > 0 ? opt.r0 : 8;
   const int rank_cap = opt.rank_cap > 0 ? opt.rank_cap : 512;
   const int max_batch = opt.max_batch > 0 ? opt.max_batch : 1;
@@ -466,6 +513,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     wd.tw1_off = p->ffts[wd.fft1].tw_off;
     wd.tw2_off = p->ffts[wd.fft2].tw_off;
   }
+  fit_horner(p);
 
   // ---- phase data on the device
   DevAllocs tmp;
@@ -728,13 +776,16 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
 
   // ---- layout of the factors and grids
   long long aoff = 0, boff = 0, gunit = 0;
+  p->ntile = (N + kTile - 1) / kTile;
+  const long long tile_pts = (long long)p->ntile * p->ntile * kTile * kTile;
   for (auto &wd : p->wedges) {
+    wd.qp = wd.q + (wd.q & 1);
     wd.alpha_off = aoff;
     wd.beta_off = boff;
     wd.grid_unit = gunit;
-    aoff += (long long)wd.q * NN;
-    boff += (long long)wd.q * wd.npts;
-    gunit += (long long)wd.m1 * wd.m2 * wd.q;
+    aoff += (long long)wd.qp * tile_pts;
+    boff += (long long)wd.qp * wd.npts;
+    gunit += (long long)wd.m1 * wd.m2 * wd.qp;
   }
   p->alpha_elems = aoff;
   p->beta_elems = boff;
@@ -743,6 +794,11 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   FIO_CK(dev_alloc(&p->d_beta, (size_t)boff * cs), "alloc beta");
   FIO_CK(dev_alloc(&p->d_grid, (size_t)gunit * max_batch * cs), "alloc grids");
   FIO_CK(dev_alloc(&p->d_fhat, (size_t)NN * max_batch * cs), "alloc spectrum");
+  FIO_CK(dev_alloc((void **)&p->d_errword, sizeof(int)), "alloc error word");
+  FIO_CK(cudaMemset(p->d_errword, 0, sizeof(int)), "clear error word");
+  // the padded rank term (t = q when q is odd) must stay exactly zero
+  FIO_CK(cudaMemset(p->d_alpha, 0, (size_t)aoff * cs), "clear alpha");
+  FIO_CK(cudaMemset(p->d_beta, 0, (size_t)boff * cs), "clear beta");
   FIO_CK(cudaMemcpy(p->d_wedges, p->wedges.data(), sizeof(WedgeDev) * L, cudaMemcpyHostToDevice), "upload wedges");
   {
     void *q = nullptr;
@@ -775,7 +831,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     if (s != FIO_OK) return s;
     FIO_CK(cudaMemcpy(d_W, sp.W.data(), sizeof(cd) * rc * q, cudaMemcpyHostToDevice), "upload W");
     FIO_CK(plan_form_alpha(d_AC, N, rc, q, d_W, wd, p->d_warp + (size_t)l * NN,
-                           (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision, 0),
+                           (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision,
+                           p->ntile, 0),
            "alpha kernel");
     FIO_CK(cudaMemcpy(d_P, sp.P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
     FIO_CK(cudaMemcpy(d_rx, sp.R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
@@ -791,6 +848,15 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
            "beta kernel");
   }
   FIO_CK(cudaDeviceSynchronize(), "plan construction");
+  {
+    // point-tile footprints for the interpolation and spread kernels
+    void *q = nullptr;
+    FIO_CK(dev_alloc(&q, sizeof(int4) * (size_t)L * p->ntile * p->ntile), "alloc tiles");
+    p->d_tiles = (int4 *)q;
+    FIO_CK(dev_alloc(&q, sizeof(uint2) * (size_t)L * tile_pts), "alloc tile-order warp");
+    p->d_warpt = (uint2 *)q;
+    FIO_CK(build_tiles(p), "tile footprints");
+  }
 
   // ---- summary
   p->q_max = 0; p->q_min = 1 << 30; p->r_max = 0;
@@ -804,7 +870,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   p->q_mean = qs / L;
   p->sep_err = 0;
   for (double e : p->wedge_err) p->sep_err = std::max(p->sep_err, e);
-  p->bytes_total = (size_t)(aoff + boff) * cs + (size_t)gunit * max_batch * cs +
+  p->bytes_total = sizeof(int4) * (size_t)L * p->ntile * p->ntile +
+                   sizeof(uint2) * (size_t)L * tile_pts + (size_t)(aoff + boff) * cs + (size_t)gunit * max_batch * cs +
                    (size_t)NN * max_batch * cs + (size_t)NN * L * sizeof(uint2) +
                    tw.size() / 2 * cs + p->rows.size() * sizeof(RowDev) +
                    p->wedges.size() * sizeof(WedgeDev) + p->ffts.size() * sizeof(FftPlanDev);

@@ -52,7 +52,8 @@ class _PlanInfo(ctypes.Structure):
                 ("bytes_warp", ctypes.c_ulonglong), ("bytes_grid", ctypes.c_ulonglong),
                 ("bytes_total", ctypes.c_ulonglong), ("grid_points", ctypes.c_ulonglong),
                 ("alg_bytes_apply", ctypes.c_ulonglong), ("plan_seconds", ctypes.c_double),
-                ("kernel_launches", ctypes.c_ulonglong), ("sep_error", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_ulonglong), ("max_footprint", ctypes.c_int),
+                ("mean_footprint", ctypes.c_double), ("sep_error", ctypes.c_double)]
 
 
 class _WedgeInfo(ctypes.Structure):
@@ -193,7 +194,8 @@ class Plan:
             raise FioError(FIO_EINVAL, f"input dtype must be {self.dtype}, got {x.dtype}")
         if x.shape[-2:] != (self.N, self.N):
             raise FioError(FIO_EINVAL, f"input must end with ({self.N}, {self.N})")
-        return x.contiguous()
+        # lazily conjugated / negated views keep unmodified memory: materialise them
+        return x.resolve_conj().resolve_neg().contiguous()
 
     def _run(self, fn, x, out, what):
         torch = self._torch
@@ -269,7 +271,7 @@ def dft2(x, inverse: bool = False, out=None):
     import torch
     if x.dtype not in (torch.complex64, torch.complex128) or not x.is_cuda:
         raise FioError(FIO_EINVAL, "dft2 needs a complex CUDA tensor")
-    x = x.contiguous()
+    x = x.resolve_conj().resolve_neg().contiguous()
     N = x.shape[-1]
     if out is None:
         out = torch.empty_like(x)

@@ -100,6 +100,7 @@ def test_tiny_grids(env, orc, N):
     with fio.Plan(N, fio.PHASE_ELLIPSE, prm, 1e-6, precision="fp64") as plan:
         out = plan.apply(dev(torch, f, "fp64")).cpu().numpy()[0]
         adj = plan.adjoint(dev(torch, f, "fp64")).cpu().numpy()[0]
+        plan.sync()
     ph = orc.Phase(orc.ELLIPSE, prm)
     assert rel(orc.apply_dense(ph, orc.Amplitude(), f[0]), out) < 1e-6
     assert rel(orc.adjoint_dense(ph, orc.Amplitude(), f[0]), adj) < 1e-6
@@ -117,6 +118,7 @@ def test_ellipse_sampled(env, orc, N, prec, eps):
     f = synth.smooth_noise_discs(N, seed=N)
     with fio.Plan(N, fio.PHASE_ELLIPSE, prm, eps, precision=prec) as plan:
         out = plan.apply(dev(torch, f[None], prec)).cpu().numpy()[0]
+        plan.sync()  # raises if an in-kernel bounds check fired
     n1, n2 = synth.sample_points(N, 512, seed=1)
     ref = orc.apply_points(orc.Phase(orc.ELLIPSE, prm), orc.Amplitude(), orc.dft2(f), n1, n2)
     assert rel(ref, out[n1, n2]) < eps
@@ -147,6 +149,8 @@ def test_tau_modes_amplitude_batch(env, orc):
         x = dev(torch, f, "mixed")
         out = plan.apply(x).cpu().numpy()
         one = plan.apply(x[5:6].clone()).cpu().numpy()
+        plan.adjoint(x)
+        plan.sync()
     assert np.array_equal(one[0], out[5])  # batching does not change the arithmetic
     ph, amp = orc.Phase(orc.TAU_MODES, prm), orc.Amplitude(1, 0.5, 0.3)
     n1, n2 = synth.sample_points(N, 256, seed=2)
