@@ -318,26 +318,52 @@ k_interp_tile(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
 
 // ------------------------------------------------------------------- S4a ---
 
+constexpr int kGrp = 8;             // rank terms per gather pass
+constexpr int kMaxSortRows = 256;   // footprints with more rows use the unsorted loop
+
+// Accumulate the contributions of point q (weight wt) to one cell for `ng` terms.
+template <typename T, int NG>
+__device__ __forceinline__ void gather_terms(Cx<T> *acc, const Cx<T> *pairs, int q, T wt) {
+#pragma unroll
+  for (int k = 0; k < NG; k += 2) {
+    const Cx<T> *pp = pairs + ((k >> 1) * 256 + q) * 2;
+    Cx<T> s0, s1;
+    if constexpr (sizeof(T) == 4) {
+      const float4 v4 = *reinterpret_cast<const float4 *>(pp);
+      s0 = Cx<T>{v4.x, v4.y};
+      s1 = Cx<T>{v4.z, v4.w};
+    } else {
+      s0 = pp[0];
+      s1 = pp[1];
+    }
+    acc[k].x += wt * s0.x;
+    acc[k].y += wt * s0.y;
+    acc[k + 1].x += wt * s1.x;
+    acc[k + 1].y += wt * s1.y;
+  }
+}
+
 template <typename T, int W>
 __global__ void __launch_bounds__(256, 2)
 k_spread_tile(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
               const WedgeDev *__restrict__ Wd, const int4 *__restrict__ tiles,
               const Cx<T> *__restrict__ alpha, const uint2 *__restrict__ warpt, int N, int L,
-              int B, int nt, KbDev kb, HornerDev hz, int smem_g, int bgmax, int *errw) {
+              int B, int nt, KbDev kb, HornerDev hz, int bgmax, int *errw) {
   using C = Cx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint4 *sG = reinterpret_cast<uint4 *>(smem_raw);  // footprint accumulator, cell-major units
-  C(*sIn)[256] = reinterpret_cast<C(*)[256]>(smem_raw + smem_g);
-  T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw + smem_g + bgmax * 256 * sizeof(C));
-  int2 *sOff = reinterpret_cast<int2 *>(smem_raw + smem_g + bgmax * 256 * sizeof(C) +
+  C(*sIn)[256] = reinterpret_cast<C(*)[256]>(smem_raw);  // [bgmax]: inputs by point
+  C *pairs = reinterpret_cast<C *>(smem_raw + bgmax * 256 * sizeof(C));  // conj(alpha) g, term pairs
+  T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw + (bgmax + kGrp) * 256 * sizeof(C));
+  int2 *sOff = reinterpret_cast<int2 *>(smem_raw + (bgmax + kGrp) * 256 * sizeof(C) +
                                         256 * 2 * W * sizeof(T));
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  int *sStart = reinterpret_cast<int *>(sOff + 256);      // bucket bounds by footprint row
+  short *sSort = reinterpret_cast<short *>(sStart + kMaxSortRows + 1);  // points sorted by row
+  const int tid = threadIdx.x;
   const int tile = blockIdx.x;
   const int I = tile / nt, J = tile % nt;
   const long long NN = (long long)N * N;
   const int nt2 = nt * nt;
   const bool valid = I * kTile + tid / kTile < N && J * kTile + tid % kTile < N;
-  constexpr int cpu = 16 / (int)sizeof(C);
   for (int b0 = 0; b0 < B; b0 += bgmax) {
     const int BG = min(bgmax, B - b0);
     __syncthreads();
@@ -350,102 +376,95 @@ k_spread_tile(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
       const WedgeDev &w = Wd[l];
       const int qp = w.qp;
       const int4 tl = tiles[(long long)l * nt2 + tile];
-      __syncthreads();
+      const bool sorted = tl.z <= kMaxSortRows;
+      __syncthreads();  // previous wedge done with sWt, sOff, sSort, pairs
       point_windows<T, W>(warpt + ((long long)l * nt2 + tile) * 256, w, tl, kb, hz, valid, sWt,
                           sOff, errw);
-      const int nu = qp / cpu;
-      const int cells = tl.z * tl.w;
-      const int umax = smem_g / 16 / cells;
-      const bool direct = umax < 1;  // footprint too large: add to global memory directly
-      const int CHU = direct ? min(nu, 32) : min(min(nu, umax), 32);
+      const int dr = sOff[tid].x;  // own entry: no barrier needed
+      if (sorted)
+        for (int r = tid; r <= tl.z; r += 256) sStart[r] = 0;
+      __syncthreads();
+      if (sorted && dr >= 0) atomicAdd(&sStart[dr + 1], 1);
+      __syncthreads();
+      if (sorted && tid == 0)
+        for (int r = 1; r <= tl.z; ++r) sStart[r] += sStart[r - 1];
+      __syncthreads();
+      if (sorted && dr >= 0) sSort[atomicAdd(&sStart[dr], 1)] = (short)tid;
+      // after the scatter sStart[r] is the end of bucket r (bucket r-1 ends where r begins)
       const long long nch = (long long)B * qp;
       C *gw = grid + w.grid_unit * B;
-      const C *al_tile = alpha + w.alpha_off + (long long)tile * 256 * qp;
+      const C *al_pt = alpha + w.alpha_off + ((long long)tile * 256 + tid) * qp;
+      const int cells = tl.z * tl.w;
       for (int bb = 0; bb < BG; ++bb) {
-        for (int u0 = 0; u0 < nu; u0 += CHU) {
-          const int nuc = min(CHU, nu - u0);
-          const long long cbase = (long long)(b0 + bb) * qp + (long long)u0 * cpu;
+        for (int t0 = 0; t0 < qp; t0 += kGrp) {
+          const int ng = min(kGrp, qp - t0);  // even
           __syncthreads();
-          if (!direct)
-            for (int e = tid; e < cells * nuc; e += 256) sG[e] = make_uint4(0, 0, 0, 0);
-          __syncthreads();
-          const int gpw = 32 / nuc;
-          const int g = lane / nuc, k = lane - g * nuc;
-          const int stride = 8 * gpw;
-          for (int r0 = 0; r0 < 256; r0 += stride) {
-            const int p = r0 + wid * gpw + g;
-            if (g >= gpw || p >= 256) continue;
-            const int2 off = sOff[p];
-            if (off.x < 0) continue;
-            const T *wp = sWt[p];
-            const int t = (u0 + k) * cpu;
-            const C gv = sIn[bb][p];
-            C c0, c1 = C{0, 0};
-            if constexpr (sizeof(T) == 4) {
-              const float4 al = *reinterpret_cast<const float4 *>(al_tile + (long long)p * qp + t);
-              c0 = cmulc(gv, C{al.x, al.y});  // g conj(alpha_t)
-              c1 = cmulc(gv, C{al.z, al.w});
-            } else {
-              c0 = cmulc(gv, al_tile[(long long)p * qp + t]);
-            }
-            for (int a1 = 0; a1 < W; ++a1) {
-              const T w1 = wp[a1];
-              for (int a2 = 0; a2 < W; ++a2) {
-                const T wt = w1 * wp[W + a2];
-                if (!direct) {
-                  T *u = reinterpret_cast<T *>(sG + ((off.x + a1) * tl.w + off.y + a2) * nuc + k);
-                  atomicAdd(u, wt * c0.x);
-                  atomicAdd(u + 1, wt * c0.y);
-                  if constexpr (sizeof(T) == 4) {
-                    atomicAdd(u + 2, wt * c1.x);
-                    atomicAdd(u + 3, wt * c1.y);
-                  }
-                } else {
-                  C *dst = gw + ((long long)((tl.x + off.x + a1) % w.m1) * w.m2 +
-                                 (tl.y + off.y + a2) % w.m2) * nch + cbase + (long long)k * cpu;
-                  if constexpr (sizeof(T) == 4) {
-                    atomicAdd(reinterpret_cast<float4 *>(dst),
-                              make_float4(wt * c0.x, wt * c0.y, wt * c1.x, wt * c1.y));
-                  } else {
-                    atomicAdd(&dst->x, wt * c0.x);
-                    atomicAdd(&dst->y, wt * c0.y);
-                  }
-                }
+          {
+            const C g = sIn[bb][tid];
+            const bool on = dr >= 0;
+            for (int k = 0; k < ng; k += 2) {
+              C a0, a1;
+              if constexpr (sizeof(T) == 4) {
+                const float4 v = *reinterpret_cast<const float4 *>(al_pt + t0 + k);
+                a0 = C{v.x, v.y};
+                a1 = C{v.z, v.w};
+              } else {
+                a0 = al_pt[t0 + k];
+                a1 = al_pt[t0 + k + 1];
               }
+              C *dst = pairs + ((k >> 1) * 256 + tid) * 2;
+              dst[0] = on ? cmulc(g, a0) : C{0, 0};  // g conj(alpha_t)
+              dst[1] = on ? cmulc(g, a1) : C{0, 0};
             }
           }
           __syncthreads();
-          if (!direct) {
-            // flush the accumulator: row by row, contiguous units, 16-byte atomics
-            for (int f1 = wid; f1 < tl.z; f1 += 8) {
-              int g1 = tl.x + f1;
-              while (g1 >= w.m1) g1 -= w.m1;
-              C *rowdst = gw + (long long)g1 * w.m2 * nch + cbase;
-              const uint4 *rowsrc = sG + f1 * tl.w * nuc;
-              const int sf2 = 32 / nuc, sk = 32 - sf2 * nuc;
-              int f2 = lane / nuc, kk = lane - (lane / nuc) * nuc;
-              for (int e = lane; e < tl.w * nuc; e += 32) {
-                const uint4 v = rowsrc[e];
-                if ((v.x | v.y | v.z | v.w) != 0u) {
-                  int g2 = tl.y + f2;
-                  while (g2 >= w.m2) g2 -= w.m2;
-                  C *dst = rowdst + (long long)g2 * nch + (long long)kk * cpu;
+          for (int cell = tid; cell < cells; cell += 256) {
+            const int r = cell / tl.w, c = cell - r * tl.w;
+            int beg = 0, end = 256;
+            if (sorted) {
+              const int rlo = r - W + 1;  // buckets rlo .. r hold the points covering row r
+              beg = rlo > 0 ? sStart[rlo - 1] : 0;
+              end = sStart[r];
+            }
+            C acc[kGrp];
+#pragma unroll
+            for (int k = 0; k < kGrp; ++k) acc[k] = C{0, 0};
+            bool any = false;
+            for (int it = beg; it < end; ++it) {
+              const int q = sorted ? (int)sSort[it] : it;
+              const int2 d = sOff[q];
+              if (d.x < 0) continue;
+              const unsigned u = (unsigned)(r - d.x), v = (unsigned)(c - d.y);
+              if (u < (unsigned)W && v < (unsigned)W) {
+                const T wt = sWt[q][u] * sWt[q][W + v];
+                any = true;
+                if (ng == kGrp) gather_terms<T, kGrp>(acc, pairs, q, wt);
+                else
+                  for (int k = 0; k < ng; k += 2) {
+                    const C *pp = pairs + ((k >> 1) * 256 + q) * 2;
+                    acc[k].x += wt * pp[0].x;
+                    acc[k].y += wt * pp[0].y;
+                    acc[k + 1].x += wt * pp[1].x;
+                    acc[k + 1].y += wt * pp[1].y;
+                  }
+              }
+            }
+            if (any) {
+              C *dst = gw + ((long long)((tl.x + r) % w.m1) * w.m2 + (tl.y + c) % w.m2) * nch +
+                       (long long)(b0 + bb) * qp + t0;
+#pragma unroll
+              for (int k = 0; k < kGrp; k += 2)
+                if (k < ng) {
                   if constexpr (sizeof(T) == 4) {
-                    atomicAdd(reinterpret_cast<float4 *>(dst),
-                              make_float4(__uint_as_float(v.x), __uint_as_float(v.y),
-                                          __uint_as_float(v.z), __uint_as_float(v.w)));
+                    atomicAdd(reinterpret_cast<float4 *>(dst + k),
+                              make_float4(acc[k].x, acc[k].y, acc[k + 1].x, acc[k + 1].y));
                   } else {
-                    atomicAdd(&dst->x, __hiloint2double((int)v.y, (int)v.x));
-                    atomicAdd(&dst->y, __hiloint2double((int)v.w, (int)v.z));
+                    atomicAdd(&dst[k].x, acc[k].x);
+                    atomicAdd(&dst[k].y, acc[k].y);
+                    atomicAdd(&dst[k + 1].x, acc[k + 1].x);
+                    atomicAdd(&dst[k + 1].y, acc[k + 1].y);
                   }
                 }
-                f2 += sf2;
-                kk += sk;
-                if (kk >= nuc) {
-                  kk -= nuc;
-                  ++f2;
-                }
-              }
             }
           }
         }
@@ -479,13 +498,15 @@ cudaError_t run_tile_kernels(const fio_plan_s *p, const void *in, void *grid, vo
   const size_t smem = tile_smem<T, W>(p, bgmax);
   cudaError_t e;
   if (spread) {
+    const size_t ssm = (size_t)(bgmax + kGrp) * 256 * sizeof(C) + 256 * 2 * W * sizeof(T) +
+                       256 * sizeof(int2) + (kMaxSortRows + 1) * sizeof(int) + 256 * sizeof(short);
     e = cudaFuncSetAttribute(k_spread_tile<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)smem);
+                             (int)ssm);
     if (e != cudaSuccess) return e;
-    k_spread_tile<T, W><<<nblk, 256, smem, s>>>((const C *)in, (C *)grid, p->d_wedges, p->d_tiles,
-                                                (const C *)p->d_alpha, p->d_warpt, p->N, p->L, B,
-                                                p->ntile, make_kbdev(p), p->horner, smem_g,
-                                                bgmax, p->d_errword);
+    k_spread_tile<T, W><<<nblk, 256, ssm, s>>>((const C *)in, (C *)grid, p->d_wedges, p->d_tiles,
+                                               (const C *)p->d_alpha, p->d_warpt, p->N, p->L, B,
+                                               p->ntile, make_kbdev(p), p->horner, bgmax,
+                                               p->d_errword);
   } else {
     e = cudaFuncSetAttribute(k_interp_tile<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
