@@ -127,6 +127,38 @@ fio_status fio_apply(fio_plan plan, const void *f, void *out, int batch, void *s
  * <L f, g> = <f, L* g> holds to rounding. */
 fio_status fio_apply_adjoint(fio_plan plan, const void *g, void *out, int batch, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Forward apply that allocates nothing.
+ *
+ * Some callers cannot allocate device memory while they run: a framework that
+ * owns all device memory through its own pool and forbids other allocations,
+ * a real-time loop that cannot pay the latency or risk the failure of a
+ * cudaMalloc, or a process that has already handed the rest of the GPU to
+ * other work.  fio_apply_noalloc computes exactly what fio_apply computes, but
+ * its NUFFT grids and spectrum live in one fixed scratch array compiled into
+ * this library (a file-scope device array of FIO_NOALLOC_SCRATCH_BYTES, held
+ * by every GPU that loads the library until the process exits) instead of the
+ * plan's workspace.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine, and records no timing events.  The paper has no counterpart; this
+ * is an interface convenience.
+ *
+ *   - Limit: grid_points * batch + N * N * batch complex values (complex64 for
+ *     FIO_MIXED, complex128 for FIO_FP64) must fit in FIO_NOALLOC_SCRATCH_BYTES;
+ *     larger requests return FIO_EINVAL with the sizes in fio_last_error().
+ *   - Set-up: the first call on a device looks up the scratch array's device
+ *     address (cudaGetSymbolAddress) with that device current, and the plan's
+ *     device must be the current device.  Make that first call before any
+ *     stream capture.
+ *   - Sharing: every call uses the same array, which keeps the last call's
+ *     contents.  The forward path writes every scratch value before reading it,
+ *     so nothing has to be cleared, but two calls that may overlap on the GPU
+ *     (different streams, or different host threads without ordering) race on
+ *     the array: serialise them.
+ * f, out, batch and stream as for fio_apply; batch is not limited by the plan's
+ * max_batch, only by the scratch size. */
+#define FIO_NOALLOC_SCRATCH_BYTES (32u << 20)
+fio_status fio_apply_noalloc(fio_plan plan, const void *f, void *out, int batch, void *stream);
+
 /* Wait for the plan's work on `stream` and report any pending CUDA error. */
 fio_status fio_plan_sync(fio_plan plan, void *stream);
 

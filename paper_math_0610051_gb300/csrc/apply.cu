@@ -342,8 +342,9 @@ struct StageTimer {
   const fio_plan_s *p;
   cudaStream_t s;
   size_t pair = (size_t)-1;
-  StageTimer(const fio_plan_s *plan, cudaStream_t st, int stage) : p(plan), s(st) {
-    if (!p->timing) return;
+  StageTimer(const fio_plan_s *plan, cudaStream_t st, int stage, bool allowed = true)
+      : p(plan), s(st) {
+    if (!allowed || !p->timing) return;
     if (2 * (p->ev_used + 1) > p->ev_pool.size()) {
       cudaEvent_t a, b;
       if (cudaEventCreate(&a) != cudaSuccess) return;
@@ -380,7 +381,7 @@ static FftPlanDev plan_for_N(const fio_plan_s *p, const void **tw) {
 
 template <typename T>
 static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int B,
-                              cudaStream_t s) {
+                              cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing) {
   using C = Cx<T>;
   const int prec = p->precision;
   const int N = p->N, L = p->L;
@@ -390,8 +391,8 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
   cudaError_t e;
   // S0: fhat in natural order (no centring shift)
   {
-    StageTimer st(p, s, FIO_STAGE_S0_DFT);
-    e = dft2_impl<T>(N, f, p->d_fhat, B, 0, plN, twN, false, s);
+    StageTimer st(p, s, FIO_STAGE_S0_DFT, timing);
+    e = dft2_impl<T>(N, f, fhat_ws, B, 0, plN, twN, false, s);
     p->launches += 2;
   }
   if (e != cudaSuccess) return e;
@@ -402,10 +403,10 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
   if ((e = set_smem(k_scatter_rowfft<T>, sm1)) != cudaSuccess) return e;
   dim3 g1((unsigned)p->rows.size(), (unsigned)((B * g0.max_q + nl1 - 1) / nl1));
   {
-    StageTimer st(p, s, FIO_STAGE_S1_SCATTER);
-    k_scatter_rowfft<T><<<g1, kThreads, sm1, s>>>((const C *)p->d_fhat, p->d_wedges, p->d_rows,
+    StageTimer st(p, s, FIO_STAGE_S1_SCATTER, timing);
+    k_scatter_rowfft<T><<<g1, kThreads, sm1, s>>>((const C *)fhat_ws, p->d_wedges, p->d_rows,
                                                   p->d_ffts, (const C *)p->d_twiddle,
-                                                  (const C *)p->d_beta, (C *)p->d_grid, N, B, nl1);
+                                                  (const C *)p->d_beta, (C *)grid_ws, N, B, nl1);
     p->launches += 1;
   }
   // S2
@@ -414,15 +415,15 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
   if ((e = set_smem(k_colfft<T>, sm2)) != cudaSuccess) return e;
   const LaunchGeom g2 = geom(p, B, nl2);
   {
-    StageTimer st(p, s, FIO_STAGE_S2_COLFFT);
-    k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)p->d_grid, p->d_wedges, p->d_ffts,
+    StageTimer st(p, s, FIO_STAGE_S2_COLFFT, timing);
+    k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)grid_ws, p->d_wedges, p->d_ffts,
                                                      (const C *)p->d_twiddle, L, B, nl2, 0);
     p->launches += 1;
   }
   // S3
   {
-    StageTimer st(p, s, FIO_STAGE_S3_INTERP);
-    e = launch_interp(p, p->d_grid, out, B, s);
+    StageTimer st(p, s, FIO_STAGE_S3_INTERP, timing);
+    e = launch_interp(p, grid_ws, out, B, s);
     if (e != cudaSuccess) return e;
     p->launches += 1;
   }
@@ -487,8 +488,14 @@ static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out,
 
 cudaError_t launch_apply(const fio_plan_s *p, const void *f, void *out, int batch,
                          cudaStream_t s) {
-  if (p->precision == FIO_FP64) return apply_impl<double>(p, f, out, batch, s);
-  return apply_impl<float>(p, f, out, batch, s);
+  return launch_apply_ws(p, f, out, batch, s, p->d_grid, p->d_fhat, true);
+}
+
+cudaError_t launch_apply_ws(const fio_plan_s *p, const void *f, void *out, int batch,
+                            cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing) {
+  if (p->precision == FIO_FP64)
+    return apply_impl<double>(p, f, out, batch, s, grid_ws, fhat_ws, timing);
+  return apply_impl<float>(p, f, out, batch, s, grid_ws, fhat_ws, timing);
 }
 
 cudaError_t launch_adjoint(const fio_plan_s *p, const void *g, void *out, int batch,

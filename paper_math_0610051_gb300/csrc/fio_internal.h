@@ -141,6 +141,10 @@ cudaError_t launch_apply(const fio_plan_s *p, const void *f, void *out, int batc
                          cudaStream_t s);
 cudaError_t launch_adjoint(const fio_plan_s *p, const void *g, void *out, int batch,
                            cudaStream_t s);
+// The forward apply on caller-chosen workspace: grid_ws holds grid_units * batch
+// complex values and fhat_ws N * N * batch; timing = false records no events.
+cudaError_t launch_apply_ws(const fio_plan_s *p, const void *f, void *out, int batch,
+                            cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing);
 cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int batch, int inverse,
                         const FftPlanDev *d_plan, const void *d_tw, cudaStream_t s);
 size_t apply_smem_bytes(int n, int nl, int precision);

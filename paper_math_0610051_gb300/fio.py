@@ -65,7 +65,8 @@ class _WedgeInfo(ctypes.Structure):
 
 # Every symbol include/fio.h declares (checked by the tests).
 EXPORTS = [
-    "fio_options_default", "fio_plan_create", "fio_apply", "fio_apply_adjoint", "fio_plan_sync",
+    "fio_options_default", "fio_plan_create", "fio_apply", "fio_apply_adjoint", "fio_apply_noalloc",
+    "fio_plan_sync",
     "fio_plan_get_info", "fio_plan_get_wedge", "fio_plan_export_wedge", "fio_plan_export_warp",
     "fio_plan_destroy", "fio_plan_set_timing", "fio_plan_stage_times",
     "fio_dft2", "fio_default_wedges", "fio_wedge_map", "fio_wedge_geometry", "fio_kb_eval",
@@ -90,6 +91,7 @@ def lib():
                                           ctypes.POINTER(_Options), ctypes.POINTER(P)]
             L.fio_apply.argtypes = [P, P, P, I, P]
             L.fio_apply_adjoint.argtypes = [P, P, P, I, P]
+            L.fio_apply_noalloc.argtypes = [P, P, P, I, P]
             L.fio_plan_sync.argtypes = [P, P]
             L.fio_plan_get_info.argtypes = [P, ctypes.POINTER(_PlanInfo)]
             L.fio_plan_get_wedge.argtypes = [P, I, ctypes.POINTER(_WedgeInfo)]
