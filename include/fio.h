@@ -39,6 +39,7 @@ extern "C" {
 #endif
 
 typedef struct fio_plan_s *fio_plan;
+typedef struct fio_surrogate_s *fio_surrogate;
 
 typedef enum {
   FIO_OK = 0,
@@ -95,6 +96,9 @@ typedef struct {
   int r0;                     /* initial sample count r; 0 = 8 */
   int rank_cap;               /* largest r before FIO_ERANK; 0 = 512 */
   int max_batch;              /* largest batch the plan's workspace holds; 0 = 1 */
+  fio_surrogate surrogate;    /* trained phase surrogate (tau-mode phases), or NULL; see below */
+  double surrogate_warp_budget; /* largest judged warp error, in cycles at |xi| = N/sqrt 2, for
+                                   which the surrogate's warped points are used; 0 = 0.5 */
 } fio_options;
 
 /* Fill *opt with the defaults listed above.  Returns FIO_EINVAL for NULL. */
@@ -159,6 +163,55 @@ fio_status fio_apply_adjoint(fio_plan plan, const void *g, void *out, int batch,
 #define FIO_NOALLOC_SCRATCH_BYTES (32u << 20)
 fio_status fio_apply_noalloc(fio_plan plan, const void *f, void *out, int batch, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Learned phase surrogate (tau-mode phases Phi = x.xi + |xi| tau(x, theta)).
+ *
+ * A 4 -> 64 -> 64 -> 3 tanh network maps (x1, x2, cos theta, sin theta) to
+ * (tau, d tau/d x1, d tau/d x2); d tau/d theta is its directional derivative.  It
+ * is trained on the GPU on `nsamples` plain evaluations (the literal sum over the
+ * modes, FP64) with Adam, BF16 tensor-core products and FP32 accumulation, then
+ * judged on 65536 held-out plain samples.
+ *
+ * fio_plan_create uses it for the warped points y_l(x) = grad_xi Phi(x, xihat_l)
+ * only when the judged warp error, in cycles at |xi| = N/sqrt 2, is within
+ * surrogate_warp_budget: any smooth warp keeps the factorisation of
+ * a exp(2 pi i Phi) exact (the residual is always formed from the plain phase),
+ * only the separation rank changes.  Its residual-phase error in cycles is
+ * reported; the plain phase stays the residual's judge and is always used.
+ *
+ * Parameter vector (FP32, fio_surrogate_nparams() values): W1[4][64], b1[64],
+ * W2[64][64], b2[64], W3[64][3], b3[3], row-major with the input index first.
+ * Outputs are scaled by tau_scale (tau) and dx_scale (x-derivatives) of
+ * fio_surrogate_info.  All pointers below are DEVICE pointers unless stated. */
+typedef struct {
+  int nparams, nsamples, epochs;
+  long long steps;
+  double train_seconds, final_loss;   /* mean squared error of the scaled outputs */
+  double tau_scale, dx_scale;
+  double heldout_tau_maxerr;          /* max |tau_net - tau| on held-out samples */
+  double heldout_dx_maxerr;           /* max over x1, x2 of the derivative errors */
+  double heldout_dtheta_maxerr;       /* max |d_theta tau_net - d_theta tau| */
+  double heldout_tau_relrms;          /* RMS error of tau relative to RMS tau */
+} fio_surrogate_info;
+
+fio_status fio_surrogate_train(const fio_phase *phase, int nsamples, int epochs, int batch,
+                               unsigned long long seed, fio_surrogate *out);
+void fio_surrogate_destroy(fio_surrogate s);
+fio_status fio_surrogate_get_info(fio_surrogate s, fio_surrogate_info *info);
+/* Copy the FP32 parameters to (set = 0) or from (set = 1) the HOST array params. */
+fio_status fio_surrogate_params(fio_surrogate s, float *params, int set);
+/* y4[i] = (tau, d tau/d x1, d tau/d x2, d tau/d theta) for x4[i] = (x1, x2, cos, sin). */
+fio_status fio_surrogate_eval(fio_surrogate s, int n, const float *x4, float *y4, void *stream);
+/* Mean squared error of the scaled outputs against t3 (n x 3, scaled targets) and
+ * its gradient with respect to the parameters (grad: nparams floats). */
+fio_status fio_surrogate_loss_grad(fio_surrogate s, int n, const float *x4, const float *t3,
+                                   float *grad, double *loss);
+/* The plain-evaluation samples the training uses: x4 (n x 4 floats) and
+ * t4 = (tau, d1, d2, d_theta) in FP64 (n x 4 doubles). */
+fio_status fio_surrogate_samples(const fio_phase *phase, int n, unsigned long long seed, float *x4,
+                                 double *t4);
+int fio_surrogate_nparams(void);
+
 /* Wait for the plan's work on `stream` and report any pending CUDA error. */
 fio_status fio_plan_sync(fio_plan plan, void *stream);
 
@@ -176,8 +229,13 @@ typedef struct {
   unsigned long long alg_bytes_apply; /* algorithmic HBM bytes of one batch-1 apply */
   double plan_seconds;              /* wall time of fio_plan_create */
   unsigned long long kernel_launches; /* this plan's kernel launches so far (all applies) */
-  int max_footprint;                /* largest grid footprint (cells) of a 16 x 16 point tile */
-  double mean_footprint;            /* mean footprint over (wedge, tile) */
+  int surrogate_warp;               /* 1 if the warped points came from the surrogate */
+  double surrogate_warp_cycles;     /* the surrogate's judged warp error (cycles), or 0 */
+  double surrogate_residual_cycles; /* its judged residual-phase error (cycles), or 0 */
+  int max_bin_points;               /* most points in one bin (the points of a wedge are sorted
+                                       by window-start cell; a bin is 16 x 16 start cells) */
+  double mean_bin_points;           /* mean points per non-empty bin */
+  int max_spread_candidates;        /* most points whose windows reach one bin's cells */
   double sep_error;                 /* largest per-wedge estimate of the relative Frobenius
                                        error of the separated factors (Sec. 4, Table 1's
                                        estimator over every column, on 200 random rows) */

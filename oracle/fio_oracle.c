@@ -230,6 +230,28 @@ void or_amp_eval(int kind, double a1, double a2, int npts, const double *x1, con
   for (int i = 0; i < npts; ++i) out[i] = amp(&a, x1[i], k1[i], k2[i]);
 }
 
+/* tau(x, theta) of the tau-mode phase and its derivatives, by the literal sum
+ * over modes: out[4 i + 0..3] = tau, d tau/d x1, d tau/d x2, d tau/d theta. */
+void or_tau_eval(int nmodes, const double *params, int npts, const double *x1, const double *x2,
+                 const double *theta, double *out) {
+  for (int i = 0; i < npts; ++i) {
+    double t = 0, d1 = 0, d2 = 0, dt = 0;
+    for (int j = 0; j < nmodes; ++j) {
+      const double *p = params + 5 * j;
+      const double arg = TWO_PI * (p[1] * x1[i] + p[2] * x2[i]) + p[3] * theta[i] + p[4];
+      const double s = sin(arg);
+      t += p[0] * cos(arg);
+      d1 -= p[0] * s * TWO_PI * p[1];
+      d2 -= p[0] * s * TWO_PI * p[2];
+      dt -= p[0] * s * p[3];
+    }
+    out[4 * i] = t;
+    out[4 * i + 1] = d1;
+    out[4 * i + 2] = d2;
+    out[4 * i + 3] = dt;
+  }
+}
+
 /* ---------------------------------------------------------------- Eq. dfio -- */
 
 /* (Lf)(x_i) at grid points x_i = (n1_i/N, n2_i/N), from the centred fhat. */

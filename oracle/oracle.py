@@ -65,6 +65,7 @@ def _load():
             lib.or_adjoint_hat_points.argtypes = [i, i, i, P, i, i, d, d, P, i, P, P, P]
             lib.or_adjoint_dense.argtypes = [i, i, i, P, i, i, d, d, P, P]
             lib.or_matrix.argtypes = [i, i, i, P, i, i, d, d, P]
+            lib.or_tau_eval.argtypes = [i, P, i, P, P, P, P]
             _lib = lib
     return _lib
 
@@ -179,6 +180,15 @@ def matrix(phase: Phase, amp: Amplitude, N: int) -> np.ndarray:
     """Dense N^2 x N^2 matrix of L (tiny N only: O(N^6))."""
     out = np.empty((N * N, N * N), np.complex128)
     _load().or_matrix(N, *phase.args(), *amp.args(), _p(out))
+    return out
+
+
+def tau_eval(modes, x1, x2, theta) -> np.ndarray:
+    """[n, 4]: tau, d tau/d x1, d tau/d x2, d tau/d theta of the tau-mode phase."""
+    modes = _c(np.asarray(modes, np.float64).ravel(), np.float64)
+    x1, x2, theta = _c(x1, np.float64), _c(x2, np.float64), _c(theta, np.float64)
+    out = np.empty((len(x1), 4), np.float64)
+    _load().or_tau_eval(len(modes) // 5, _p(modes), len(x1), _p(x1), _p(x2), _p(theta), _p(out))
     return out
 
 

@@ -133,8 +133,8 @@ fio_status fio_plan_sync(fio_plan p, void *stream) {
   e = cudaMemcpy(&word, p->d_errword, sizeof(int), cudaMemcpyDeviceToHost);
   if (e != cudaSuccess) return cuda_fail(e, "fio_plan_sync");
   if (word != 0) {
-    set_error("fio_plan_sync: an in-kernel bounds check failed (a point window left its tile "
-              "footprint); the affected terms were skipped");
+    set_error("fio_plan_sync: an in-kernel consistency check failed (a point's window start "
+              "left the bin it was sorted into); the affected terms were skipped");
     return FIO_ECUDA;
   }
   return FIO_OK;
@@ -166,8 +166,12 @@ fio_status fio_plan_get_info(fio_plan p, fio_plan_info *info) {
   info->plan_seconds = p->plan_seconds;
   info->sep_error = p->sep_err;
   info->kernel_launches = p->launches;
-  info->max_footprint = p->max_foot;
-  info->mean_footprint = p->mean_foot;
+  info->surrogate_warp = p->sur_warp;
+  info->surrogate_warp_cycles = p->sur_warp_cycles;
+  info->surrogate_residual_cycles = p->sur_residual_cycles;
+  info->max_bin_points = p->max_bin_pts;
+  info->mean_bin_points = p->mean_bin_pts;
+  info->max_spread_candidates = p->max_cand;
   return FIO_OK;
 }
 
@@ -247,24 +251,25 @@ fio_status fio_plan_export_wedge(fio_plan p, int l, double *alpha, double *beta,
     return cudaSuccess;
   };
   if (alpha) {
-    // stored in tile order [tile][point][t]: gamma^x * exp(2 pi i y'.xi_c) / N --
+    // stored in sorted point order [pos][t]: gamma^x * exp(2 pi i y'.xi_c) / N --
     // undo the centre factor and 1/N
-    const long long tp = (long long)p->ntile * p->ntile * 256;
     std::vector<cd> a;
-    cudaError_t e = fetch(p->d_alpha, w.alpha_off, (long long)w.qp * tp, a);
+    cudaError_t e = fetch(p->d_alpha, w.alpha_off, (long long)w.qp * NN, a);
     if (e != cudaSuccess) return cuda_fail(e, "export alpha");
     std::vector<uint2> Y((size_t)NN);
     e = cudaMemcpy(Y.data(), p->d_warp + (size_t)l * NN, sizeof(uint2) * NN, cudaMemcpyDeviceToHost);
     if (e != cudaSuccess) return cuda_fail(e, "export warp");
-    for (long long x = 0; x < NN; ++x) {
-      const int n1 = (int)(x / p->N), n2 = (int)(x % p->N);
-      const long long tile = (long long)(n1 >> 4) * p->ntile + (n2 >> 4);
-      const int pt = (n1 & 15) * 16 + (n2 & 15);
+    std::vector<uint32_t> perm((size_t)NN);
+    e = cudaMemcpy(perm.data(), p->d_perm + (size_t)l * NN, sizeof(uint32_t) * NN,
+                   cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) return cuda_fail(e, "export point order");
+    for (long long pos = 0; pos < NN; ++pos) {
+      const long long x = perm[pos];
       const uint32_t yk = Y[x].x * (uint32_t)w.xc1 + Y[x].y * (uint32_t)w.xc2;
       const double ang = 2.0 * M_PI * ((double)yk * 2.3283064365386962890625e-10);
       const cd undo = std::polar((double)p->N, -ang);
       for (int t = 0; t < w.q; ++t) {
-        const cd v = a[(size_t)((tile * 256 + pt) * w.qp + t)] * undo;
+        const cd v = a[(size_t)(pos * w.qp + t)] * undo;
         alpha[2 * ((size_t)t * NN + x)] = v.real();
         alpha[2 * ((size_t)t * NN + x) + 1] = v.imag();
       }

@@ -439,9 +439,7 @@ static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out,
   const long long NN = (long long)N * N;
   cudaError_t e;
   const size_t cs = prec == FIO_FP64 ? 16 : 8;
-  // S4a
-  e = cudaMemsetAsync(p->d_grid, 0, (size_t)p->grid_units * B * cs, s);
-  if (e != cudaSuccess) return e;
+  // S4a (writes every grid cell)
   {
     StageTimer st(p, s, FIO_STAGE_S4A_SPREAD);
     e = launch_spread(p, gin, p->d_grid, B, s);

@@ -39,11 +39,23 @@ struct WedgeDev {
   int fft1, fft2;         // FftPlanDev index for lengths m1, m2
   int row_off;            // first RowDev of this wedge
   long long grid_unit;    // grid offset in units of complex * batch: sum_{l'<l} m1 m2 qp
-  long long alpha_off;    // complex offset of alpha[l][0][0] (layout [t][x])
+  long long alpha_off;    // complex offset of alpha[l][0][0] (layout [pos][t])
   long long beta_off;     // complex offset of beta[l][0][0]  (layout [t][p])
   int pt_off;             // first point of this wedge in the global point order
   int tw1_off, tw2_off;   // twiddle offsets for m1 / m2 (copies of the FftPlanDev fields)
+  int nb1, nb2;           // bins of kBin x kBin window-start cells per grid axis
+  long long key_off;      // first entry of this wedge's bucket table (nb1 nb2 kBin^2 + 1 ints)
 };
+
+// Points of a wedge are sorted by the grid cell where their KB window starts,
+// bin by bin (kBin x kBin start cells, row-major inside a bin), so that the
+// points of one bin touch only a (kBin + w - 1)^2 cell footprint.
+constexpr int kBin = 16;
+
+// The bucket-table key of window-start cell (s1, s2) of a wedge with nb2 bins per row.
+__host__ __device__ inline long long bin_key(int s1, int s2, int nb2) {
+  return ((long long)(s1 / kBin) * nb2 + s2 / kBin) * (kBin * kBin) + (s1 % kBin) * kBin + s2 % kBin;
+}
 
 // Piecewise-polynomial KB weights for the FP32 path: with z = u - j0 - (w/2 - 1)
 // in [0, 1) and t = 2z - 1, phi(u - j0 - a) = sum_k c[k][a] t^k.
@@ -78,6 +90,8 @@ struct fio_plan_s {
   fio::KbParams kb{};
   int q_max = 0, q_min = 0, r_max = 0;
   double sep_err = 0;
+  int sur_warp = 0;
+  double sur_warp_cycles = 0, sur_residual_cycles = 0;
   double q_mean = 0;
   int device = 0;
 
@@ -97,19 +111,22 @@ struct fio_plan_s {
   fio::RowDev *d_rows = nullptr;
   fio::FftPlanDev *d_ffts = nullptr;
   void *d_twiddle = nullptr;      // complex (float2 / double2) exp(-2 pi i k/n) tables
-  void *d_alpha = nullptr;        // gamma^x * centre phase / N, [l][tile][point][t]
+  void *d_alpha = nullptr;        // gamma^x * centre phase / N, [l][pos][t] (sorted point order)
   void *d_beta = nullptr;         // gamma^xi / phihat, [l][t][p]
   uint2 *d_warp = nullptr;        // warped points y' mod 1 as 32-bit fractions, [l][x]
-  uint2 *d_warpt = nullptr;       // the same in tile order, [l][tile][point]
+  uint2 *d_warps = nullptr;       // the same in sorted point order, [l][pos]
+  uint32_t *d_perm = nullptr;     // sorted position -> x = n1 N + n2, [l][pos]
+  int *d_cstart = nullptr;        // per wedge: first sorted position of every bucket key (+ end)
+  int4 *d_items = nullptr;        // interpolation work: (l, bin, first pos, end pos)
+  int2 *d_bins = nullptr;         // spread work: (l, bin), every bin of every wedge
+  int n_items = 0, n_bins = 0;
   fio::HornerDev horner{};
   void *d_grid = nullptr;         // NUFFT grids [l][g1][g2][b*q + t]
   void *d_fhat = nullptr;         // spectrum workspace, batch * N * N complex
-  int4 *d_tiles = nullptr;        // per (wedge, 16x16 point tile): grid footprint (r0, c0, F1, F2)
   int *d_errword = nullptr;       // set by a kernel whose in-kernel bounds check fails
-  int ntile = 0;                  // tiles per grid side
-  int max_foot = 0;               // largest F1 * F2 over all (wedge, tile)
-  int foot_p99 = 0;               // 99th percentile of the padded footprint plane (16-byte units)
-  double mean_foot = 0;           // mean F1 * F2
+  int max_bin_pts = 0;            // most points in one bin
+  double mean_bin_pts = 0;        // mean points per non-empty bin
+  int max_cand = 0;               // most points whose windows reach one bin's cells
   size_t bytes_total = 0;
   unsigned long long alg_bytes = 0;
 
@@ -149,8 +166,12 @@ cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int bat
                         const FftPlanDev *d_plan, const void *d_tw, cudaStream_t s);
 size_t apply_smem_bytes(int n, int nl, int precision);
 // interp.cu
-constexpr int kTile = 16;  // point tiles of kTile x kTile grid points
-cudaError_t build_tiles(fio_plan_s *p);   // fills d_tiles, max_foot, d_warpt (synchronises)
+constexpr int kItemPts = 1024;  // most points of one interpolation work item
+// Sort wedge l's points by window-start cell: fills d_perm[l], d_warps[l], the
+// bucket table at d_cstart + key_off (synchronises; host counting sort, stable in x).
+cudaError_t sort_wedge_points(fio_plan_s *p, int l, std::vector<int> &cstart_host);
+// Work lists and bin statistics from every wedge's bucket table.
+cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> &cstart);
 void fit_horner(fio_plan_s *p);           // host: piecewise-polynomial KB weights
 cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B, cudaStream_t s);
 cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s);
@@ -177,10 +198,11 @@ cudaError_t plan_eval_cols(const PhaseDev &ph, const void *d_xdata, int N, const
 // Gram matrix G = A_C^H A_C (r x r), deterministic two-level reduction.
 cudaError_t plan_gram(const double2 *d_AC, long long rows, int r, double2 *d_partial,
                       int nparts, double2 *d_G, cudaStream_t s);
-// alpha[tile][t][lane] = (sum_c A_C[x][c] W[c][t]) * exp(2 pi i y'.xi_c) / N  (W = V S^-1, r x q)
+// alpha[pos][t] = (sum_c A_C[x][c] W[c][t]) * exp(2 pi i y'.xi_c) / N with x = perm[pos]
+// (W = V S^-1, r x q)
 cudaError_t plan_form_alpha(const double2 *d_AC, int N, int r, int q, const double2 *d_W,
-                            const WedgeDev &w, const uint2 *d_warp_l, void *d_alpha_l,
-                            int precision, int ntile, cudaStream_t s);
+                            const WedgeDev &w, const uint2 *d_warp_l, const uint32_t *d_perm_l,
+                            void *d_alpha_l, int precision, cudaStream_t s);
 // beta[t][p] = (sum_i P[t][i] A(x_i, xi_p)) * dec[p], P = U_R^+ (q x r),
 // dec[p] = 1 / (phihat(xi'_1/m1) phihat(xi'_2/m2)) (NUFFT deconvolution)
 cudaError_t plan_form_beta(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
@@ -188,16 +210,16 @@ cudaError_t plan_form_beta(const PhaseDev &ph, const void *d_xdata, int N, const
                            const double2 *d_P, const int *d_pk1, const int *d_pk2,
                            const double *d_dec, void *d_beta_l, int precision, cudaStream_t s);
 
-// Per-column squared error of U T against A on s sampled rows (validation).
-cudaError_t plan_validate(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
-                          const uint2 *d_warp_l, const int *d_gx, int s, const double2 *d_UG,
-                          const double2 *d_T, int q, const int *d_pk1, const int *d_pk2,
-                          double *d_err, double *d_nrm, cudaStream_t st);
+// surrogate.cu: warped points from a trained surrogate, and its judged errors.
+cudaError_t surrogate_warp(const fio_surrogate_s *s, int N, int L, const WedgeDev *d_w,
+                           uint2 *d_warp);
+const fio_surrogate_info *surrogate_info(const fio_surrogate_s *s);
 
 // Per-column squared error of U T against A on s sampled rows (validation).
 cudaError_t plan_validate(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
                           const uint2 *d_warp_l, const int *d_gx, int s, const double2 *d_UG,
                           const double2 *d_T, int q, const int *d_pk1, const int *d_pk2,
                           double *d_err, double *d_nrm, cudaStream_t st);
+
 
 }  // namespace fio

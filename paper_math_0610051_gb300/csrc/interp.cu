@@ -1,25 +1,30 @@
 // interp.cu -- S3 (type-2 interpolation with the gamma^x multiply and the sums
 // over rank terms and wedges, Sec. 3.4 steps 3-4) and S4a (the type-1 spread of
-// the adjoint, Sec. 3.5 steps 1-2) on 16 x 16 point tiles.
+// the adjoint, Sec. 3.5 steps 1-2), on bins of the NUFFT grid.
 //
-// A CTA owns one point tile and walks over every wedge.  For wedge l the tile's
-// warped points y'_l(x) m fall in a small box of the NUFFT grid (the tile
-// footprint, fixed by the plan), which is staged in shared memory cell-major:
-// the rank terms of a cell are one contiguous run of 16-byte units (two
-// complex64 terms, or one complex128).
+// The plan sorts every wedge's points by the grid cell where their KB window
+// starts, bin by bin (kBin x kBin start cells).  The warped points of a wedge
+// are a smooth but strongly sheared image of the x grid, so neighbouring x give
+// scattered windows; neighbouring sorted points give overlapping ones.  The
+// points of one bin touch only its (kBin + w - 1)^2 cell footprint.
 //
-// The interpolation is warp-cooperative: a group of lanes owns one point, one
-// lane per unit, so the group's loads of a cell are one contiguous run (free of
-// bank conflicts) and the warped windows of different points never collide in
-// a lane.  Per-point KB weights are computed once per wedge into shared memory;
-// the gamma^x multiply is folded in per lane and the sum over rank terms is a
-// segmented shuffle reduction.  The spread is the mirror image: each group adds
-// its point's weighted values to a shared footprint accumulator (distinct units
-// per lane), which is then added to the grid with 16-byte vector atomics
-// (neighbouring tiles' footprints overlap).
+// S3: a CTA takes a work item (wedge, bin, up to kItemPts sorted points),
+// stages the bin's footprint in shared memory cell-major (the rank terms of a
+// cell are one contiguous run of 16-byte units: two complex64 terms or one
+// complex128), and interpolates warp-cooperatively: a group of lanes owns one
+// point, one lane per unit, so a group's loads of a cell are one contiguous run.
+// The gamma^x multiply is folded in per lane, the sum over rank terms is a
+// segmented shuffle reduction, and the sum over wedges is a vector atomic add
+// into the output (each output receives one add per wedge).
 //
-// Every point checks that its window lies inside the footprint; a violation is
-// recorded in the plan's error word and the point is skipped.
+// S4a: a CTA owns the kBin x kBin cells of one bin and gathers, for each of
+// them, the contributions of every point whose window covers it: the points
+// whose start cell lies in the (kBin + w - 1)^2 region above and left of the
+// bin, found through the plan's bucket table.  Every grid cell is written once,
+// by its own bin, with no atomics and no clearing of the grid.
+//
+// A point whose window start disagrees with the bucket it was sorted into is
+// recorded in the plan's error word and skipped.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -32,63 +37,34 @@ namespace fio {
 
 namespace {
 
-constexpr int kBG = 8;                 // inputs accumulated together per pass
-constexpr int kSmemG = 48 * 1024;      // default footprint staging buffer
-constexpr int kSmemGMax = 160 * 1024;  // largest staging buffer
 constexpr unsigned kFull = 0xffffffffu;
+constexpr int kInterpSmemG = 96 * 1024;   // footprint staging buffer of S3
+constexpr int kSpreadSmem = 100 * 1024;   // dynamic shared memory budget of S4a
+constexpr int kCand = 256;                // candidate points per S4a chunk
+constexpr int kMaxRegion = (kBin + kMaxKbWidth - 1) * (kBin + kMaxKbWidth - 1);
 
-// ------------------------------------------------------- tile footprints ---
+int host_mod(int a, int m) {
+  const int r = a % m;
+  return r < 0 ? r + m : r;
+}
 
-__global__ void __launch_bounds__(256) k_tiles(const WedgeDev *__restrict__ Wd,
-                                               const uint2 *__restrict__ warp, int N, int nt,
-                                               int kbw, int4 *__restrict__ tiles,
-                                               uint2 *__restrict__ warpt) {
-  __shared__ int ref[2], lo[2], hi[2];
-  const int nt2 = nt * nt;
-  const int l = blockIdx.x / nt2, tile = blockIdx.x % nt2;
-  const int I = tile / nt, J = tile % nt;
-  const int tid = threadIdx.x;
-  const long long NN = (long long)N * N;
-  const WedgeDev w = Wd[l];
-  const int n1 = I * kTile + tid / kTile, n2 = J * kTile + tid % kTile;
-  const bool valid = n1 < N && n2 < N;
-  float bdum;
-  if (tid == 0) {
-    const uint2 Y = warp[l * NN + (long long)(I * kTile) * N + J * kTile];
-    ref[0] = kb_first<float>(Y.x, w.m1, kbw, &bdum);
-    ref[1] = kb_first<float>(Y.y, w.m2, kbw, &bdum);
-    lo[0] = lo[1] = 1 << 30;
-    hi[0] = hi[1] = -(1 << 30);
-  }
-  __syncthreads();
-  uint2 Y = make_uint2(0, 0);
-  if (valid) {
-    Y = warp[l * NN + (long long)n1 * N + n2];
-    const int m[2] = {w.m1, w.m2};
-    const int j[2] = {kb_first<float>(Y.x, w.m1, kbw, &bdum), kb_first<float>(Y.y, w.m2, kbw, &bdum)};
-    for (int d = 0; d < 2; ++d) {
-      // offset from the reference point, centred in [-m/2, m/2)
-      const int o = imodp(j[d] - ref[d] + m[d] / 2, m[d]) - m[d] / 2;
-      atomicMin(&lo[d], o);
-      atomicMax(&hi[d], o);
-    }
-  }
-  warpt[(long long)blockIdx.x * 256 + tid] = Y;  // tile order: [l][tile][point]
-  __syncthreads();
-  if (tid == 0) {
-    const int m[2] = {w.m1, w.m2};
-    int r[2], F[2];
-    for (int d = 0; d < 2; ++d) {
-      F[d] = hi[d] - lo[d] + kbw;
-      if (2 * F[d] >= m[d]) {  // spread too wide to centre unambiguously: take every row
-        r[d] = 0;
-        F[d] = m[d] + kbw - 1;
-      } else {
-        r[d] = imodp(ref[d] + lo[d], m[d]);
-      }
-    }
-    tiles[blockIdx.x] = make_int4(r[0], r[1], F[0], F[1]);
-  }
+// ------------------------------------------------------------ point sort ---
+
+__global__ void k_keys(const uint2 *__restrict__ warp_l, long long NN, WedgeDev w, int kbw,
+                       uint32_t *__restrict__ keys) {
+  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (x >= NN) return;
+  const uint2 Y = warp_l[x];
+  float b;
+  const int s1 = imodp(kb_first<float>(Y.x, w.m1, kbw, &b), w.m1);
+  const int s2 = imodp(kb_first<float>(Y.y, w.m2, kbw, &b), w.m2);
+  keys[x] = (uint32_t)bin_key(s1, s2, w.nb2);
+}
+
+__global__ void k_gather_warp(const uint2 *__restrict__ warp_l, const uint32_t *__restrict__ perm_l,
+                              long long NN, uint2 *__restrict__ out) {
+  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos < NN) out[pos] = warp_l[perm_l[pos]];
 }
 
 // ------------------------------------------------------------- helpers -----
@@ -111,32 +87,16 @@ __device__ __forceinline__ void kb_weights(T base, const KbDev &kb, const Horner
   }
 }
 
-// Phase 1 of both kernels: thread p computes its point's window offsets inside
-// the tile footprint and its 2W weights into shared memory (off = -1: skip).
+// Window start cell (s1, s2) of a warped point and its 2W weights.
 template <typename T, int W>
-__device__ __forceinline__ void point_windows(const uint2 *__restrict__ warpt_tile, const WedgeDev &w,
-                                              int4 tl, const KbDev &kb, const HornerDev &hz,
-                                              bool valid, T (*sWt)[2 * W], int2 *sOff, int *errw) {
-  const int p = threadIdx.x;
-  int2 off = make_int2(-1, -1);
-  if (valid) {
-    T b1, b2;
-    const uint2 Y = warpt_tile[p];
-    const int j01 = kb_first<T>(Y.x, w.m1, W, &b1);
-    const int j02 = kb_first<T>(Y.y, w.m2, W, &b2);
-    T w1[W], w2[W];
-    kb_weights<T, W>(b1, kb, hz, w1);
-    kb_weights<T, W>(b2, kb, hz, w2);
-#pragma unroll
-    for (int a = 0; a < W; ++a) {
-      sWt[p][a] = w1[a];
-      sWt[p][W + a] = w2[a];
-    }
-    const int dr = imodp(j01 - tl.x, w.m1), dc = imodp(j02 - tl.y, w.m2);
-    if (dr + W <= tl.z && dc + W <= tl.w) off = make_int2(dr, dc);
-    else atomicOr(errw, 1);
-  }
-  sOff[p] = off;
+__device__ __forceinline__ int2 point_weights(uint2 Y, int m1, int m2, const KbDev &kb,
+                                              const HornerDev &hz, T *wt) {
+  T b1, b2;
+  const int j01 = kb_first<T>(Y.x, m1, W, &b1);
+  const int j02 = kb_first<T>(Y.y, m2, W, &b2);
+  kb_weights<T, W>(b1, kb, hz, wt);
+  kb_weights<T, W>(b2, kb, hz, wt + W);
+  return make_int2(imodp(j01, m1), imodp(j02, m2));
 }
 
 // Copy `nu` units (starting at complex channel cbase) of every footprint cell into
@@ -177,294 +137,283 @@ __device__ __forceinline__ T group_sum(T v, int k, int nu) {
   return v;
 }
 
+__device__ __forceinline__ void add_out(float2 *o, float re, float im) {
+  atomicAdd(o, make_float2(re, im));
+}
+__device__ __forceinline__ void add_out(double2 *o, double re, double im) {
+  atomicAdd(&o->x, re);
+  atomicAdd(&o->y, im);
+}
+
 // -------------------------------------------------------------------- S3 ---
 
 template <typename T, int W>
 __global__ void __launch_bounds__(256, 2)
-k_interp_tile(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
-              const int4 *__restrict__ tiles, const Cx<T> *__restrict__ alpha,
-              const uint2 *__restrict__ warpt, Cx<T> *__restrict__ out, int N, int L, int B,
-              int nt, KbDev kb, HornerDev hz, int smem_g, int bgmax, int *errw) {
+k_interp_bin(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
+             const int4 *__restrict__ items, const Cx<T> *__restrict__ alpha,
+             const uint2 *__restrict__ warps, const uint32_t *__restrict__ perm,
+             Cx<T> *__restrict__ out, long long NN, int B, KbDev kb, HornerDev hz, int smem_g,
+             int *errw) {
   using C = Cx<T>;
   extern __shared__ __align__(16) unsigned char smem_raw[];
   uint4 *sG = reinterpret_cast<uint4 *>(smem_raw);
-  C(*sAcc)[256] = reinterpret_cast<C(*)[256]>(smem_raw + smem_g);
-  T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw + smem_g + bgmax * 256 * sizeof(C));
-  int2 *sOff = reinterpret_cast<int2 *>(smem_raw + smem_g + bgmax * 256 * sizeof(C) +
-                                        256 * 2 * W * sizeof(T));
+  T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw + smem_g);
+  int2 *sOff = reinterpret_cast<int2 *>(smem_raw + smem_g + 256 * 2 * W * sizeof(T));
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  const int tile = blockIdx.x;
-  const int I = tile / nt, J = tile % nt;
-  const long long NN = (long long)N * N;
-  const int nt2 = nt * nt;
-  const bool valid = I * kTile + tid / kTile < N && J * kTile + tid % kTile < N;
+  const int4 it = items[blockIdx.x];
+  const int l = it.x;
+  const int m1 = Wd[l].m1, m2 = Wd[l].m2, nb2 = Wd[l].nb2, qp = Wd[l].qp;
   constexpr int cpu = 16 / (int)sizeof(C);  // rank terms per 16-byte unit
-  for (int b0 = 0; b0 < B; b0 += bgmax) {
-    const int BG = min(bgmax, B - b0);
-    for (int bb = 0; bb < BG; ++bb) sAcc[bb][tid] = C{0, 0};
-    for (int l = 0; l < L; ++l) {
-      const WedgeDev &w = Wd[l];
-      const int qp = w.qp;
-      const int4 tl = tiles[(long long)l * nt2 + tile];
-      __syncthreads();  // previous wedge done with sWt, sOff, sG
-      point_windows<T, W>(warpt + ((long long)l * nt2 + tile) * 256, w, tl, kb, hz, valid, sWt,
-                          sOff, errw);
-      const int nu = qp / cpu;
-      const int cells = tl.z * tl.w;
-      const int umax = smem_g / 16 / cells;     // units per cell that fit the buffer
-      const bool direct = umax < 1;             // footprint too large: read global memory
-      const int CHU = direct ? min(nu, 32) : min(min(nu, umax), 32);
-      const long long nch = (long long)B * qp;
-      const C *gw = grid + w.grid_unit * B;
-      const C *al_tile = alpha + w.alpha_off + (long long)tile * 256 * qp;
-      for (int bb = 0; bb < BG; ++bb) {
-        for (int u0 = 0; u0 < nu; u0 += CHU) {
-          const int nuc = min(CHU, nu - u0);
-          const long long cbase = (long long)(b0 + bb) * qp + (long long)u0 * cpu;
-          __syncthreads();
-          if (!direct) stage_cells<T>(sG, gw, tl, w.m1, w.m2, nch, cbase, nuc);
-          __syncthreads();
-          const int gpw = 32 / nuc;               // point groups per warp
-          const int g = lane / nuc, k = lane - g * nuc;
-          const int stride = 8 * gpw;
-          for (int r0 = 0; r0 < 256; r0 += stride) {
-            const int p = r0 + wid * gpw + g;
-            const bool act = g < gpw && p < 256;
-            const int2 off = act ? sOff[p] : make_int2(-1, -1);
-            T re = 0, im = 0;
-            if (off.x >= 0) {
-              const T *wp = sWt[p];
-              const int t = (u0 + k) * cpu;
-              if constexpr (sizeof(T) == 4) {
-                float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+  const int nu = qp / cpu;
+  const int r0 = (it.y / nb2) * kBin, c0 = (it.y % nb2) * kBin;
+  const int H1 = min(kBin, m1 - r0), H2 = min(kBin, m2 - c0);
+  const int4 tl = make_int4(r0, c0, H1 + W - 1, H2 + W - 1);
+  const int CHU = min(min(nu, 32), smem_g / 16 / (tl.z * tl.w));
+  const long long nch = (long long)B * qp;
+  const C *gw = grid + Wd[l].grid_unit * B;
+  const C *al = alpha + Wd[l].alpha_off;
+  const uint2 *ws = warps + (long long)l * NN;
+  const uint32_t *pm = perm + (long long)l * NN;
+  for (int b = 0; b < B; ++b) {
+    for (int u0 = 0; u0 < nu; u0 += CHU) {
+      const int nuc = min(CHU, nu - u0);
+      const long long cbase = (long long)b * qp + (long long)u0 * cpu;
+      __syncthreads();  // the previous pass is done with sG
+      stage_cells<T>(sG, gw, tl, m1, m2, nch, cbase, nuc);
+      const int gpw = 32 / nuc;  // point groups per warp
+      const int g = lane / nuc, k = lane - g * nuc;
+      const int stride = 8 * gpw;
+      for (int c = it.z; c < it.w; c += 256) {
+        const int np = min(256, it.w - c);
+        __syncthreads();  // footprint staged; the previous chunk is done with sWt, sOff
+        if (tid < np) {
+          int2 off = make_int2(-1, -1);
+          const int2 sc = point_weights<T, W>(ws[c + tid], m1, m2, kb, hz, sWt[tid]);
+          const int dr = sc.x - r0, dc = sc.y - c0;
+          if (dr >= 0 && dr < H1 && dc >= 0 && dc < H2) off = make_int2(dr, dc);
+          else atomicOr(errw, 1);
+          sOff[tid] = off;
+        }
+        __syncthreads();
+        for (int q0 = 0; q0 < np; q0 += stride) {
+          const int pi = q0 + wid * gpw + g;
+          const bool act = g < gpw && pi < np;
+          const int2 off = act ? sOff[pi] : make_int2(-1, -1);
+          T re = 0, im = 0;
+          if (off.x >= 0) {
+            const T *wp = sWt[pi];
+            const int t = (u0 + k) * cpu;
+            const C *al_pt = al + (long long)(c + pi) * qp + t;
+            if constexpr (sizeof(T) == 4) {
+              float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
 #pragma unroll
-                for (int a1 = 0; a1 < W; ++a1) {
-                  float rax = 0.f, ray = 0.f, rbx = 0.f, rby = 0.f;
-                  const float w1 = wp[a1];
-                  if (!direct) {
-                    const float4 *pr =
-                        reinterpret_cast<const float4 *>(sG) + ((off.x + a1) * tl.w + off.y) * nuc + k;
+              for (int a1 = 0; a1 < W; ++a1) {
+                float rax = 0.f, ray = 0.f, rbx = 0.f, rby = 0.f;
+                const float4 *pr =
+                    reinterpret_cast<const float4 *>(sG) + ((off.x + a1) * tl.w + off.y) * nuc + k;
 #pragma unroll
-                    for (int a2 = 0; a2 < W; ++a2) {
-                      const float4 gv = pr[a2 * nuc];
-                      const float w2 = wp[W + a2];
-                      rax = fmaf(w2, gv.x, rax);
-                      ray = fmaf(w2, gv.y, ray);
-                      rbx = fmaf(w2, gv.z, rbx);
-                      rby = fmaf(w2, gv.w, rby);
-                    }
-                  } else {
-                    const long long rowoff = (long long)((tl.x + off.x + a1) % w.m1) * w.m2;
-                    for (int a2 = 0; a2 < W; ++a2) {
-                      const float4 gv = *reinterpret_cast<const float4 *>(
-                          gw + (rowoff + (tl.y + off.y + a2) % w.m2) * nch + cbase + 2 * k);
-                      const float w2 = wp[W + a2];
-                      rax = fmaf(w2, gv.x, rax);
-                      ray = fmaf(w2, gv.y, ray);
-                      rbx = fmaf(w2, gv.z, rbx);
-                      rby = fmaf(w2, gv.w, rby);
-                    }
-                  }
-                  ax = fmaf(w1, rax, ax);
-                  ay = fmaf(w1, ray, ay);
-                  bx = fmaf(w1, rbx, bx);
-                  by = fmaf(w1, rby, by);
+                for (int a2 = 0; a2 < W; ++a2) {
+                  const float4 gv = pr[a2 * nuc];
+                  const float w2 = wp[W + a2];
+                  rax = fmaf(w2, gv.x, rax);
+                  ray = fmaf(w2, gv.y, ray);
+                  rbx = fmaf(w2, gv.z, rbx);
+                  rby = fmaf(w2, gv.w, rby);
                 }
-                const float4 al = *reinterpret_cast<const float4 *>(al_tile + (long long)p * qp + t);
-                re = al.x * ax - al.y * ay + al.z * bx - al.w * by;
-                im = al.x * ay + al.y * ax + al.z * by + al.w * bx;
-              } else {
-                double ax = 0.0, ay = 0.0;
-                for (int a1 = 0; a1 < W; ++a1) {
-                  double rax = 0.0, ray = 0.0;
-                  const double w1 = wp[a1];
-                  const long long rowoff = direct ? (long long)((tl.x + off.x + a1) % w.m1) * w.m2 : 0;
-#pragma unroll
-                  for (int a2 = 0; a2 < W; ++a2) {
-                    const double2 gv =
-                        direct ? gw[(rowoff + (tl.y + off.y + a2) % w.m2) * nch + cbase + k]
-                               : reinterpret_cast<const double2 *>(sG)[((off.x + a1) * tl.w + off.y + a2) * nuc + k];
-                    const double w2 = wp[W + a2];
-                    rax = fma(w2, gv.x, rax);
-                    ray = fma(w2, gv.y, ray);
-                  }
-                  ax = fma(w1, rax, ax);
-                  ay = fma(w1, ray, ay);
-                }
-                const C al = al_tile[(long long)p * qp + t];
-                re = al.x * ax - al.y * ay;
-                im = al.x * ay + al.y * ax;
+                const float w1 = wp[a1];
+                ax = fmaf(w1, rax, ax);
+                ay = fmaf(w1, ray, ay);
+                bx = fmaf(w1, rbx, bx);
+                by = fmaf(w1, rby, by);
               }
-            }
-            re = group_sum(re, k, nuc);
-            im = group_sum(im, k, nuc);
-            if (act && k == 0 && off.x >= 0) {
-              sAcc[bb][p].x += re;
-              sAcc[bb][p].y += im;
+              const float4 a = *reinterpret_cast<const float4 *>(al_pt);
+              re = a.x * ax - a.y * ay + a.z * bx - a.w * by;
+              im = a.x * ay + a.y * ax + a.z * by + a.w * bx;
+            } else {
+              double ax = 0.0, ay = 0.0;
+#pragma unroll
+              for (int a1 = 0; a1 < W; ++a1) {
+                double rax = 0.0, ray = 0.0;
+                const double2 *pr =
+                    reinterpret_cast<const double2 *>(sG) + ((off.x + a1) * tl.w + off.y) * nuc + k;
+#pragma unroll
+                for (int a2 = 0; a2 < W; ++a2) {
+                  const double2 gv = pr[a2 * nuc];
+                  const double w2 = wp[W + a2];
+                  rax = fma(w2, gv.x, rax);
+                  ray = fma(w2, gv.y, ray);
+                }
+                const double w1 = wp[a1];
+                ax = fma(w1, rax, ax);
+                ay = fma(w1, ray, ay);
+              }
+              const C a = *al_pt;
+              re = a.x * ax - a.y * ay;
+              im = a.x * ay + a.y * ax;
             }
           }
+          re = group_sum(re, k, nuc);
+          im = group_sum(im, k, nuc);
+          if (act && k == 0 && off.x >= 0) add_out(out + (long long)b * NN + pm[c + pi], re, im);
         }
       }
-    }
-    __syncthreads();
-    {
-      const int n1 = I * kTile + tid / 16, n2 = J * kTile + tid % 16;
-      if (n1 < N && n2 < N)
-        for (int bb = 0; bb < BG; ++bb)
-          out[(long long)(b0 + bb) * NN + (long long)n1 * N + n2] = sAcc[bb][tid];
     }
   }
 }
 
 // ------------------------------------------------------------------- S4a ---
 
-constexpr int kGrp = 8;             // rank terms per gather pass
-constexpr int kMaxSortRows = 256;   // footprints with more rows use the unsorted loop
-
-// Accumulate the contributions of point q (weight wt) to one cell for `ng` terms.
-template <typename T, int NG>
-__device__ __forceinline__ void gather_terms(Cx<T> *acc, const Cx<T> *pairs, int q, T wt) {
-#pragma unroll
-  for (int k = 0; k < NG; k += 2) {
-    const Cx<T> *pp = pairs + ((k >> 1) * 256 + q) * 2;
-    Cx<T> s0, s1;
-    if constexpr (sizeof(T) == 4) {
-      const float4 v4 = *reinterpret_cast<const float4 *>(pp);
-      s0 = Cx<T>{v4.x, v4.y};
-      s1 = Cx<T>{v4.z, v4.w};
-    } else {
-      s0 = pp[0];
-      s1 = pp[1];
-    }
-    acc[k].x += wt * s0.x;
-    acc[k].y += wt * s0.y;
-    acc[k + 1].x += wt * s1.x;
-    acc[k + 1].y += wt * s1.y;
-  }
-}
-
 template <typename T, int W>
 __global__ void __launch_bounds__(256, 2)
-k_spread_tile(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
-              const WedgeDev *__restrict__ Wd, const int4 *__restrict__ tiles,
-              const Cx<T> *__restrict__ alpha, const uint2 *__restrict__ warpt, int N, int L,
-              int B, int nt, KbDev kb, HornerDev hz, int bgmax, int *errw) {
+k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
+             const WedgeDev *__restrict__ Wd, const int2 *__restrict__ bins,
+             const int *__restrict__ cstart, const Cx<T> *__restrict__ alpha,
+             const uint2 *__restrict__ warps, const uint32_t *__restrict__ perm, long long NN,
+             int B, KbDev kb, HornerDev hz, int chu, int *errw) {
   using C = Cx<T>;
+  __shared__ int sRS[kMaxRegion + 1];  // region-ordered first candidate of every start cell
+  __shared__ int sGB[kMaxRegion];      // sorted position of every start cell's first point
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  C(*sIn)[256] = reinterpret_cast<C(*)[256]>(smem_raw);  // [bgmax]: inputs by point
-  C *pairs = reinterpret_cast<C *>(smem_raw + bgmax * 256 * sizeof(C));  // conj(alpha) g, term pairs
-  T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw + (bgmax + kGrp) * 256 * sizeof(C));
-  int2 *sOff = reinterpret_cast<int2 *>(smem_raw + (bgmax + kGrp) * 256 * sizeof(C) +
-                                        256 * 2 * W * sizeof(T));
-  int *sStart = reinterpret_cast<int *>(sOff + 256);      // bucket bounds by footprint row
-  short *sSort = reinterpret_cast<short *>(sStart + kMaxSortRows + 1);  // points sorted by row
-  const int tid = threadIdx.x;
-  const int tile = blockIdx.x;
-  const int I = tile / nt, J = tile % nt;
-  const long long NN = (long long)N * N;
-  const int nt2 = nt * nt;
-  const bool valid = I * kTile + tid / kTile < N && J * kTile + tid % kTile < N;
-  for (int b0 = 0; b0 < B; b0 += bgmax) {
-    const int BG = min(bgmax, B - b0);
-    __syncthreads();
-    {
-      const int n1 = I * kTile + tid / 16, n2 = J * kTile + tid % 16;
-      for (int bb = 0; bb < BG; ++bb)
-        sIn[bb][tid] = valid ? gin[(long long)(b0 + bb) * NN + (long long)n1 * N + n2] : C{0, 0};
+  T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw);
+  C *sIn = reinterpret_cast<C *>(smem_raw + kCand * 2 * W * sizeof(T));
+  int *sPos = reinterpret_cast<int *>(sIn + kCand);
+  unsigned char *sCol = reinterpret_cast<unsigned char *>(sPos + kCand);
+  uint4 *sV = reinterpret_cast<uint4 *>(
+      smem_raw + ((kCand * (2 * W * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16));
+  uint4 *sAcc = sV + kCand * chu;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  const int2 it = bins[blockIdx.x];
+  const int l = it.x;
+  const int m1 = Wd[l].m1, m2 = Wd[l].m2, nb2 = Wd[l].nb2, qp = Wd[l].qp;
+  constexpr int cpu = 16 / (int)sizeof(C);
+  const int nu = qp / cpu;
+  const int r0 = (it.y / nb2) * kBin, c0 = (it.y % nb2) * kBin;
+  const int H1 = min(kBin, m1 - r0), H2 = min(kBin, m2 - c0);
+  const int RW = H2 + W - 1, RC = (H1 + W - 1) * RW;
+  const int *cs = cstart + Wd[l].key_off;
+  const long long nch = (long long)B * qp;
+  C *gw = grid + Wd[l].grid_unit * B;
+  const C *al = alpha + Wd[l].alpha_off;
+  const uint2 *ws = warps + (long long)l * NN;
+  const uint32_t *pm = perm + (long long)l * NN;
+
+  // Start cells (r0 - W + 1 + ri, c0 - W + 1 + rj) of the region, row-major:
+  // their buckets, then an exclusive scan of the bucket sizes.
+  for (int i = tid; i < RC; i += 256) {
+    const int ri = i / RW, rj = i - ri * RW;
+    const int s1 = imodp(r0 - (W - 1) + ri, m1), s2 = imodp(c0 - (W - 1) + rj, m2);
+    const long long key = bin_key(s1, s2, nb2);
+    const int beg = cs[key];
+    sGB[i] = beg;
+    sRS[i] = cs[key + 1] - beg;
+  }
+  __syncthreads();
+  if (wid == 0) {
+    const int per = (RC + 31) / 32;
+    const int a = min(RC, lane * per), e = min(RC, a + per);
+    int sum = 0;
+    for (int i = a; i < e; ++i) sum += sRS[i];
+    int inc = sum;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+      const int v = __shfl_up_sync(kFull, inc, off);
+      if (lane >= off) inc += v;
     }
-    for (int l = 0; l < L; ++l) {
-      const WedgeDev &w = Wd[l];
-      const int qp = w.qp;
-      const int4 tl = tiles[(long long)l * nt2 + tile];
-      const bool sorted = tl.z <= kMaxSortRows;
-      __syncthreads();  // previous wedge done with sWt, sOff, sSort, pairs
-      point_windows<T, W>(warpt + ((long long)l * nt2 + tile) * 256, w, tl, kb, hz, valid, sWt,
-                          sOff, errw);
-      const int dr = sOff[tid].x;  // own entry: no barrier needed
-      if (sorted)
-        for (int r = tid; r <= tl.z; r += 256) sStart[r] = 0;
-      __syncthreads();
-      if (sorted && dr >= 0) atomicAdd(&sStart[dr + 1], 1);
-      __syncthreads();
-      if (sorted && tid == 0)
-        for (int r = 1; r <= tl.z; ++r) sStart[r] += sStart[r - 1];
-      __syncthreads();
-      if (sorted && dr >= 0) sSort[atomicAdd(&sStart[dr], 1)] = (short)tid;
-      // after the scatter sStart[r] is the end of bucket r (bucket r-1 ends where r begins)
-      const long long nch = (long long)B * qp;
-      C *gw = grid + w.grid_unit * B;
-      const C *al_pt = alpha + w.alpha_off + ((long long)tile * 256 + tid) * qp;
-      const int cells = tl.z * tl.w;
-      for (int bb = 0; bb < BG; ++bb) {
-        for (int t0 = 0; t0 < qp; t0 += kGrp) {
-          const int ng = min(kGrp, qp - t0);  // even
-          __syncthreads();
-          {
-            const C g = sIn[bb][tid];
-            const bool on = dr >= 0;
-            for (int k = 0; k < ng; k += 2) {
-              C a0, a1;
-              if constexpr (sizeof(T) == 4) {
-                const float4 v = *reinterpret_cast<const float4 *>(al_pt + t0 + k);
-                a0 = C{v.x, v.y};
-                a1 = C{v.z, v.w};
-              } else {
-                a0 = al_pt[t0 + k];
-                a1 = al_pt[t0 + k + 1];
-              }
-              C *dst = pairs + ((k >> 1) * 256 + tid) * 2;
-              dst[0] = on ? cmulc(g, a0) : C{0, 0};  // g conj(alpha_t)
-              dst[1] = on ? cmulc(g, a1) : C{0, 0};
-            }
+    int run = inc - sum;
+    for (int i = a; i < e; ++i) {
+      const int cnt = sRS[i];
+      sRS[i] = run;
+      run += cnt;
+    }
+    if (lane == 31) sRS[RC] = inc;
+  }
+  __syncthreads();
+  const int total = sRS[RC];
+  const int nchunks = max(1, (total + kCand - 1) / kCand);
+
+  for (int b = 0; b < B; ++b) {
+    for (int u0 = 0; u0 < nu; u0 += chu) {
+      const int nuc = min(chu, nu - u0);
+      const int gpw = 32 / nuc, g = lane / nuc, k = lane - g * nuc, ngr = 8 * gpw;
+      for (int ch = 0; ch < nchunks; ++ch) {
+        const int c = ch * kCand;
+        const int np = max(0, min(kCand, total - c));
+        __syncthreads();  // the previous chunk is done with the candidate arrays
+        if (tid < np) {
+          const int idx = c + tid;
+          int lo = 0, hi = RC - 1;  // the start cell holding candidate idx
+          while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (sRS[mid] <= idx) lo = mid;
+            else hi = mid - 1;
           }
-          __syncthreads();
-          for (int cell = tid; cell < cells; cell += 256) {
-            const int r = cell / tl.w, c = cell - r * tl.w;
-            int beg = 0, end = 256;
-            if (sorted) {
-              const int rlo = r - W + 1;  // buckets rlo .. r hold the points covering row r
-              beg = rlo > 0 ? sStart[rlo - 1] : 0;
-              end = sStart[r];
-            }
-            C acc[kGrp];
+          const int pos = sGB[lo] + (idx - sRS[lo]);
+          const int ri = lo / RW, rj = lo - ri * RW;
+          const int2 sc = point_weights<T, W>(ws[pos], m1, m2, kb, hz, sWt[tid]);
+          if (sc.x != imodp(r0 - (W - 1) + ri, m1) || sc.y != imodp(c0 - (W - 1) + rj, m2)) {
+            atomicOr(errw, 1);
 #pragma unroll
-            for (int k = 0; k < kGrp; ++k) acc[k] = C{0, 0};
-            bool any = false;
-            for (int it = beg; it < end; ++it) {
-              const int q = sorted ? (int)sSort[it] : it;
-              const int2 d = sOff[q];
-              if (d.x < 0) continue;
-              const unsigned u = (unsigned)(r - d.x), v = (unsigned)(c - d.y);
-              if (u < (unsigned)W && v < (unsigned)W) {
-                const T wt = sWt[q][u] * sWt[q][W + v];
-                any = true;
-                if (ng == kGrp) gather_terms<T, kGrp>(acc, pairs, q, wt);
-                else
-                  for (int k = 0; k < ng; k += 2) {
-                    const C *pp = pairs + ((k >> 1) * 256 + q) * 2;
-                    acc[k].x += wt * pp[0].x;
-                    acc[k].y += wt * pp[0].y;
-                    acc[k + 1].x += wt * pp[1].x;
-                    acc[k + 1].y += wt * pp[1].y;
-                  }
-              }
-            }
-            if (any) {
-              C *dst = gw + ((long long)((tl.x + r) % w.m1) * w.m2 + (tl.y + c) % w.m2) * nch +
-                       (long long)(b0 + bb) * qp + t0;
-#pragma unroll
-              for (int k = 0; k < kGrp; k += 2)
-                if (k < ng) {
-                  if constexpr (sizeof(T) == 4) {
-                    atomicAdd(reinterpret_cast<float4 *>(dst + k),
-                              make_float4(acc[k].x, acc[k].y, acc[k + 1].x, acc[k + 1].y));
-                  } else {
-                    atomicAdd(&dst[k].x, acc[k].x);
-                    atomicAdd(&dst[k].y, acc[k].y);
-                    atomicAdd(&dst[k + 1].x, acc[k + 1].x);
-                    atomicAdd(&dst[k + 1].y, acc[k + 1].y);
-                  }
+            for (int a = 0; a < 2 * W; ++a) sWt[tid][a] = T(0);
+          }
+          sPos[tid] = pos;
+          sCol[tid] = (unsigned char)rj;
+          sIn[tid] = gin[(long long)b * NN + pm[pos]];
+        }
+        __syncthreads();
+        // conj(alpha_t) g for units u0 .. u0 + nuc of every candidate
+        for (int e = tid; e < np * nuc; e += 256) {
+          const int t = e / nuc, kk = e - t * nuc;
+          const C gv = sIn[t];
+          const C *ap = al + (long long)sPos[t] * qp + (u0 + kk) * cpu;
+          if constexpr (sizeof(T) == 4) {
+            const float4 a = *reinterpret_cast<const float4 *>(ap);
+            const C v0 = cmulc(gv, C{a.x, a.y}), v1 = cmulc(gv, C{a.z, a.w});
+            reinterpret_cast<float4 *>(sV)[t * nuc + kk] = make_float4(v0.x, v0.y, v1.x, v1.y);
+          } else {
+            reinterpret_cast<double2 *>(sV)[t * nuc + kk] = cmulc(gv, *ap);
+          }
+        }
+        __syncthreads();
+        if (g < gpw) {
+          for (int cell = wid * gpw + g; cell < H1 * H2; cell += ngr) {
+            const int rl = cell / H2, cl = cell - rl * H2;
+            if constexpr (sizeof(T) == 4) {
+              float4 acc = ch == 0 ? make_float4(0.f, 0.f, 0.f, 0.f)
+                                   : reinterpret_cast<const float4 *>(sAcc)[cell * nuc + k];
+              for (int a1 = 0; a1 < W; ++a1) {
+                const int rb = (rl + W - 1 - a1) * RW + cl;
+                const int lo = max(sRS[rb] - c, 0), hi = min(sRS[rb + W] - c, np);
+                for (int t = lo; t < hi; ++t) {
+                  const float wt = sWt[t][a1] * sWt[t][W + cl + W - 1 - sCol[t]];
+                  const float4 v = reinterpret_cast<const float4 *>(sV)[t * nuc + k];
+                  acc.x = fmaf(wt, v.x, acc.x);
+                  acc.y = fmaf(wt, v.y, acc.y);
+                  acc.z = fmaf(wt, v.z, acc.z);
+                  acc.w = fmaf(wt, v.w, acc.w);
                 }
+              }
+              if (ch == nchunks - 1)
+                *reinterpret_cast<float4 *>(gw + ((long long)(r0 + rl) * m2 + c0 + cl) * nch +
+                                            (long long)b * qp + (u0 + k) * cpu) = acc;
+              else
+                reinterpret_cast<float4 *>(sAcc)[cell * nuc + k] = acc;
+            } else {
+              double2 acc = ch == 0 ? make_double2(0.0, 0.0)
+                                    : reinterpret_cast<const double2 *>(sAcc)[cell * nuc + k];
+              for (int a1 = 0; a1 < W; ++a1) {
+                const int rb = (rl + W - 1 - a1) * RW + cl;
+                const int lo = max(sRS[rb] - c, 0), hi = min(sRS[rb + W] - c, np);
+                for (int t = lo; t < hi; ++t) {
+                  const double wt = sWt[t][a1] * sWt[t][W + cl + W - 1 - sCol[t]];
+                  const double2 v = reinterpret_cast<const double2 *>(sV)[t * nuc + k];
+                  acc.x = fma(wt, v.x, acc.x);
+                  acc.y = fma(wt, v.y, acc.y);
+                }
+              }
+              if (ch == nchunks - 1)
+                gw[((long long)(r0 + rl) * m2 + c0 + cl) * nch + (long long)b * qp + (u0 + k)] = acc;
+              else
+                reinterpret_cast<double2 *>(sAcc)[cell * nuc + k] = acc;
             }
           }
         }
@@ -475,46 +424,46 @@ k_spread_tile(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
 
 // ------------------------------------------------------------- launchers ---
 
-int smem_g_for(const fio_plan_s *p) {
-  // room for the 99th-percentile footprint with two units per cell (larger ones
-  // use fewer units per pass, or global memory), within [kSmemG, kSmemGMax]
-  const long long need = 16LL * 2 * ((long long)p->foot_p99 + 1);
-  return (int)std::min<long long>(kSmemGMax, std::max<long long>(kSmemG, (need + 15) / 16 * 16));
+template <typename T>
+int max_units(const fio_plan_s *p) {
+  int nu = 1;
+  for (const WedgeDev &w : p->wedges) nu = std::max(nu, w.qp * (int)sizeof(T) / 8);
+  return nu;  // 16-byte units per cell: qp / 2 complex64 terms or qp complex128 terms
 }
 
 template <typename T, int W>
-size_t tile_smem(const fio_plan_s *p, int bgmax) {
-  return (size_t)smem_g_for(p) + (size_t)bgmax * 256 * sizeof(Cx<T>) + 256 * 2 * W * sizeof(T) +
-         256 * sizeof(int2);
-}
-
-template <typename T, int W>
-cudaError_t run_tile_kernels(const fio_plan_s *p, const void *in, void *grid, void *out, int B,
-                             bool spread, cudaStream_t s) {
+cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, void *out, int B,
+                            bool spread, cudaStream_t s) {
   using C = Cx<T>;
-  const int nblk = p->ntile * p->ntile;
-  const int smem_g = smem_g_for(p);
-  const int bgmax = std::min(B, kBG);
-  const size_t smem = tile_smem<T, W>(p, bgmax);
+  const long long NN = (long long)p->N * p->N;
+  const int numax = std::min(32, max_units<T>(p));
   cudaError_t e;
   if (spread) {
-    const size_t ssm = (size_t)(bgmax + kGrp) * 256 * sizeof(C) + 256 * 2 * W * sizeof(T) +
-                       256 * sizeof(int2) + (kMaxSortRows + 1) * sizeof(int) + 256 * sizeof(short);
-    e = cudaFuncSetAttribute(k_spread_tile<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             (int)ssm);
-    if (e != cudaSuccess) return e;
-    k_spread_tile<T, W><<<nblk, 256, ssm, s>>>((const C *)in, (C *)grid, p->d_wedges, p->d_tiles,
-                                               (const C *)p->d_alpha, p->d_warpt, p->N, p->L, B,
-                                               p->ntile, make_kbdev(p), p->horner, bgmax,
-                                               p->d_errword);
-  } else {
-    e = cudaFuncSetAttribute(k_interp_tile<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    const size_t fixed = (kCand * (2 * W * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16;
+    const size_t per_unit = (size_t)(kCand + kBin * kBin) * 16;
+    const int chu = (int)std::max<long long>(
+        1, std::min<long long>(numax, ((long long)kSpreadSmem - (long long)fixed) / (long long)per_unit));
+    const size_t smem = fixed + per_unit * chu;
+    e = cudaFuncSetAttribute(k_spread_bin<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    k_interp_tile<T, W><<<nblk, 256, smem, s>>>((const C *)grid, p->d_wedges, p->d_tiles,
-                                                (const C *)p->d_alpha, p->d_warpt, (C *)out, p->N,
-                                                p->L, B, p->ntile, make_kbdev(p), p->horner,
-                                                smem_g, bgmax, p->d_errword);
+    k_spread_bin<T, W><<<p->n_bins, 256, smem, s>>>(
+        (const C *)in, (C *)grid, p->d_wedges, p->d_bins, p->d_cstart, (const C *)p->d_alpha,
+        p->d_warps, p->d_perm, NN, B, make_kbdev(p), p->horner, chu, p->d_errword);
+  } else {
+    e = cudaMemsetAsync(out, 0, sizeof(C) * (size_t)NN * B, s);
+    if (e != cudaSuccess) return e;
+    const int cells = (kBin + W - 1) * (kBin + W - 1);
+    const int chu = std::max(1, std::min(numax, kInterpSmemG / (16 * cells)));
+    const int smem_g = chu * 16 * cells;
+    const size_t smem = (size_t)smem_g + 256 * 2 * W * sizeof(T) + 256 * sizeof(int2);
+    e = cudaFuncSetAttribute(k_interp_bin<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+    if (e != cudaSuccess) return e;
+    if (p->n_items > 0)
+      k_interp_bin<T, W><<<p->n_items, 256, smem, s>>>(
+          (const C *)grid, p->d_wedges, p->d_items, (const C *)p->d_alpha, p->d_warps, p->d_perm,
+          (C *)out, NN, B, make_kbdev(p), p->horner, smem_g, p->d_errword);
   }
   return cudaGetLastError();
 }
@@ -523,45 +472,97 @@ template <typename T>
 cudaError_t dispatch_w(const fio_plan_s *p, const void *in, void *grid, void *out, int B,
                        bool spread, cudaStream_t s) {
   switch (p->kb.w) {
-    case 3: return run_tile_kernels<T, 3>(p, in, grid, out, B, spread, s);
-    case 4: return run_tile_kernels<T, 4>(p, in, grid, out, B, spread, s);
-    case 5: return run_tile_kernels<T, 5>(p, in, grid, out, B, spread, s);
-    case 6: return run_tile_kernels<T, 6>(p, in, grid, out, B, spread, s);
-    case 7: return run_tile_kernels<T, 7>(p, in, grid, out, B, spread, s);
-    case 8: return run_tile_kernels<T, 8>(p, in, grid, out, B, spread, s);
-    case 9: return run_tile_kernels<T, 9>(p, in, grid, out, B, spread, s);
-    case 10: return run_tile_kernels<T, 10>(p, in, grid, out, B, spread, s);
-    case 11: return run_tile_kernels<T, 11>(p, in, grid, out, B, spread, s);
-    case 12: return run_tile_kernels<T, 12>(p, in, grid, out, B, spread, s);
+    case 3: return run_bin_kernels<T, 3>(p, in, grid, out, B, spread, s);
+    case 4: return run_bin_kernels<T, 4>(p, in, grid, out, B, spread, s);
+    case 5: return run_bin_kernels<T, 5>(p, in, grid, out, B, spread, s);
+    case 6: return run_bin_kernels<T, 6>(p, in, grid, out, B, spread, s);
+    case 7: return run_bin_kernels<T, 7>(p, in, grid, out, B, spread, s);
+    case 8: return run_bin_kernels<T, 8>(p, in, grid, out, B, spread, s);
+    case 9: return run_bin_kernels<T, 9>(p, in, grid, out, B, spread, s);
+    case 10: return run_bin_kernels<T, 10>(p, in, grid, out, B, spread, s);
+    case 11: return run_bin_kernels<T, 11>(p, in, grid, out, B, spread, s);
+    case 12: return run_bin_kernels<T, 12>(p, in, grid, out, B, spread, s);
   }
   return cudaErrorNotSupported;
 }
 
 }  // namespace
 
-cudaError_t build_tiles(fio_plan_s *p) {
-  const int nt2 = p->ntile * p->ntile;
-  k_tiles<<<p->L * nt2, 256>>>(p->d_wedges, p->d_warp, p->N, p->ntile, p->kb.w, p->d_tiles,
-                               p->d_warpt);
-  cudaError_t e = cudaGetLastError();
+cudaError_t sort_wedge_points(fio_plan_s *p, int l, std::vector<int> &cs) {
+  const WedgeDev &w = p->wedges[l];
+  const long long NN = (long long)p->N * p->N;
+  const long long nkeys = (long long)w.nb1 * w.nb2 * kBin * kBin;
+  uint32_t *d_keys = nullptr;
+  cudaError_t e = cudaMalloc(&d_keys, sizeof(uint32_t) * NN);
   if (e != cudaSuccess) return e;
-  std::vector<int4> t((size_t)p->L * nt2);
-  e = cudaMemcpy(t.data(), p->d_tiles, sizeof(int4) * t.size(), cudaMemcpyDeviceToHost);
+  k_keys<<<(unsigned)((NN + 255) / 256), 256>>>(p->d_warp + l * NN, NN, w, p->kb.w, d_keys);
+  std::vector<uint32_t> keys((size_t)NN);
+  e = cudaGetLastError();
+  if (e == cudaSuccess)
+    e = cudaMemcpy(keys.data(), d_keys, sizeof(uint32_t) * NN, cudaMemcpyDeviceToHost);
+  cudaFree(d_keys);
   if (e != cudaSuccess) return e;
-  // padded plane sizes (16-byte units) of every footprint
-  std::vector<int> planes;
-  planes.reserve(t.size());
-  double sum = 0;
-  p->max_foot = 0;
-  for (const int4 &v : t) {
-    p->max_foot = std::max(p->max_foot, v.z * v.w);
-    sum += (double)v.z * v.w;
-    planes.push_back(v.z * v.w);
+  // stable counting sort: equal keys keep increasing x
+  cs.assign((size_t)nkeys + 1, 0);
+  for (long long x = 0; x < NN; ++x) ++cs[keys[x] + 1];
+  for (long long k = 0; k < nkeys; ++k) cs[k + 1] += cs[k];
+  std::vector<uint32_t> perm((size_t)NN);
+  std::vector<int> next(cs.begin(), cs.end() - 1);
+  for (long long x = 0; x < NN; ++x) perm[next[keys[x]]++] = (uint32_t)x;
+  e = cudaMemcpy(p->d_perm + l * NN, perm.data(), sizeof(uint32_t) * NN, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(p->d_cstart + w.key_off, cs.data(), sizeof(int) * cs.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  k_gather_warp<<<(unsigned)((NN + 255) / 256), 256>>>(p->d_warp + l * NN, p->d_perm + l * NN, NN,
+                                                       p->d_warps + l * NN);
+  return cudaGetLastError();
+}
+
+cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> &cstart) {
+  std::vector<int4> items;
+  std::vector<int2> bins;
+  const int W = p->kb.w;
+  long long nonempty = 0, total = 0;
+  int maxb = 0;
+  long long maxc = 0;
+  for (int l = 0; l < p->L; ++l) {
+    const WedgeDev &w = p->wedges[l];
+    const std::vector<int> &cs = cstart[l];
+    for (int bin = 0; bin < w.nb1 * w.nb2; ++bin) {
+      const int beg = cs[(size_t)bin * kBin * kBin], end = cs[(size_t)(bin + 1) * kBin * kBin];
+      for (int c = beg; c < end; c += kItemPts) items.push_back(make_int4(l, bin, c, std::min(end, c + kItemPts)));
+      bins.push_back(make_int2(l, bin));
+      if (end > beg) {
+        ++nonempty;
+        total += end - beg;
+      }
+      maxb = std::max(maxb, end - beg);
+      const int r0 = (bin / w.nb2) * kBin, c0 = (bin % w.nb2) * kBin;
+      const int RH = std::min(kBin, w.m1 - r0) + W - 1, RW = std::min(kBin, w.m2 - c0) + W - 1;
+      long long cand = 0;
+      for (int i = 0; i < RH; ++i) {
+        const int s1 = host_mod(r0 - (W - 1) + i, w.m1);
+        for (int j = 0; j < RW; ++j) {
+          const long long k = bin_key(s1, host_mod(c0 - (W - 1) + j, w.m2), w.nb2);
+          cand += cs[k + 1] - cs[k];
+        }
+      }
+      maxc = std::max(maxc, cand);
+    }
   }
-  std::sort(planes.begin(), planes.end());
-  p->foot_p99 = planes[std::min(planes.size() - 1, (size_t)(0.99 * planes.size()))];  // cells
-  p->mean_foot = sum / (double)t.size();
-  return cudaSuccess;
+  p->n_items = (int)items.size();
+  p->n_bins = (int)bins.size();
+  p->max_bin_pts = maxb;
+  p->mean_bin_pts = nonempty ? (double)total / nonempty : 0.0;
+  p->max_cand = (int)maxc;
+  cudaError_t e = cudaMalloc(&p->d_items, sizeof(int4) * std::max<size_t>(1, items.size()));
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&p->d_bins, sizeof(int2) * std::max<size_t>(1, bins.size()));
+  if (e != cudaSuccess) return e;
+  if (!items.empty())
+    e = cudaMemcpy(p->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return e;
+  return cudaMemcpy(p->d_bins, bins.data(), sizeof(int2) * bins.size(), cudaMemcpyHostToDevice);
 }
 
 cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B,

@@ -319,16 +319,16 @@ fio_status cuda_status(cudaError_t e, const char *what) {
   } while (0)
 
 void free_plan_device(fio_plan_s *p) {
-  void *ptrs[] = {p->d_wedges, p->d_rows, p->d_ffts,  p->d_twiddle, p->d_alpha,  p->d_beta,
-                  p->d_warp,   p->d_grid, p->d_fhat, p->d_tiles,   p->d_errword, p->d_warpt};
+  void *ptrs[] = {p->d_wedges, p->d_rows,  p->d_ffts,    p->d_twiddle, p->d_alpha,
+                  p->d_beta,   p->d_warp,  p->d_grid,    p->d_fhat,    p->d_errword,
+                  p->d_warps,  p->d_perm,  p->d_cstart,  p->d_items,   p->d_bins};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   p->d_wedges = nullptr; p->d_rows = nullptr; p->d_ffts = nullptr; p->d_twiddle = nullptr;
   p->d_alpha = nullptr; p->d_beta = nullptr; p->d_warp = nullptr; p->d_grid = nullptr;
-  p->d_fhat = nullptr;
-  p->d_tiles = nullptr;
-  p->d_errword = nullptr;
-  p->d_warpt = nullptr;
+  p->d_fhat = nullptr; p->d_errword = nullptr;
+  p->d_warps = nullptr; p->d_perm = nullptr; p->d_cstart = nullptr; p->d_items = nullptr;
+  p->d_bins = nullptr;
 }
 
 // Piecewise polynomials of the KB kernel on the w unit intervals of a window:
@@ -545,6 +545,20 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   }
   FIO_CK(dev_alloc((void **)&p->d_warp, (size_t)NN * L * sizeof(uint2)), "alloc warp");
   FIO_CK(plan_warp(ph, d_xdata, N, L, p->d_wedges, p->d_warp, 0), "warp kernel");
+  if (opt.surrogate && phase->kind == FIO_PHASE_TAU_MODES) {
+    // the surrogate's warped points, if its judged error is within budget: the
+    // residual below always uses the plain phase, so the factorisation of
+    // a exp(2 pi i Phi) stays exact and only the rank can change
+    const fio_surrogate_info *si = surrogate_info(opt.surrogate);
+    const double xi_max = N / std::sqrt(2.0);
+    p->sur_warp_cycles = xi_max * (si->heldout_tau_maxerr + si->heldout_dtheta_maxerr);
+    p->sur_residual_cycles = xi_max * si->heldout_tau_maxerr;
+    const double budget = opt.surrogate_warp_budget > 0 ? opt.surrogate_warp_budget : 0.5;
+    if (p->sur_warp_cycles <= budget) {
+      FIO_CK(surrogate_warp(opt.surrogate, N, L, p->d_wedges, p->d_warp), "surrogate warp");
+      p->sur_warp = 1;
+    }
+  }
 
   // ---- pass 1: randomized separation rank per wedge (Sec. 3.2)
   p->wedge_r.assign(L, 0);
@@ -775,17 +789,19 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   }
 
   // ---- layout of the factors and grids
-  long long aoff = 0, boff = 0, gunit = 0;
-  p->ntile = (N + kTile - 1) / kTile;
-  const long long tile_pts = (long long)p->ntile * p->ntile * kTile * kTile;
+  long long aoff = 0, boff = 0, gunit = 0, koff = 0;
   for (auto &wd : p->wedges) {
     wd.qp = wd.q + (wd.q & 1);
     wd.alpha_off = aoff;
     wd.beta_off = boff;
     wd.grid_unit = gunit;
-    aoff += (long long)wd.qp * tile_pts;
+    wd.nb1 = (wd.m1 + kBin - 1) / kBin;
+    wd.nb2 = (wd.m2 + kBin - 1) / kBin;
+    wd.key_off = koff;
+    aoff += (long long)wd.qp * NN;
     boff += (long long)wd.qp * wd.npts;
     gunit += (long long)wd.m1 * wd.m2 * wd.qp;
+    koff += (long long)wd.nb1 * wd.nb2 * kBin * kBin + 1;
   }
   p->alpha_elems = aoff;
   p->beta_elems = boff;
@@ -794,6 +810,9 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   FIO_CK(dev_alloc(&p->d_beta, (size_t)boff * cs), "alloc beta");
   FIO_CK(dev_alloc(&p->d_grid, (size_t)gunit * max_batch * cs), "alloc grids");
   FIO_CK(dev_alloc(&p->d_fhat, (size_t)NN * max_batch * cs), "alloc spectrum");
+  FIO_CK(dev_alloc((void **)&p->d_perm, sizeof(uint32_t) * (size_t)NN * L), "alloc point order");
+  FIO_CK(dev_alloc((void **)&p->d_warps, sizeof(uint2) * (size_t)NN * L), "alloc sorted warp");
+  FIO_CK(dev_alloc((void **)&p->d_cstart, sizeof(int) * (size_t)koff), "alloc bucket tables");
   FIO_CK(dev_alloc((void **)&p->d_errword, sizeof(int)), "alloc error word");
   FIO_CK(cudaMemset(p->d_errword, 0, sizeof(int)), "clear error word");
   // the padded rank term (t = q when q is odd) must stay exactly zero
@@ -823,16 +842,18 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     fio_status s = scratch((void **)&d_dec, sizeof(double) * (size_t)maxnpts, "alloc deconvolution");
     if (s != FIO_OK) return s;
   }
+  std::vector<std::vector<int>> cstart(L);
   for (int l = 0; l < L; ++l) {
     const WedgeDev &wd = p->wedges[l];
     const Sep &sp = sep[l];
     const int rc = (int)sp.C.size(), q = sp.q, nr = (int)sp.R.size();
+    FIO_CK(sort_wedge_points(p, l, cstart[l]), "point sort");
     fio_status s = eval_cols(l, sp.C);
     if (s != FIO_OK) return s;
     FIO_CK(cudaMemcpy(d_W, sp.W.data(), sizeof(cd) * rc * q, cudaMemcpyHostToDevice), "upload W");
     FIO_CK(plan_form_alpha(d_AC, N, rc, q, d_W, wd, p->d_warp + (size_t)l * NN,
-                           (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision,
-                           p->ntile, 0),
+                           p->d_perm + (size_t)l * NN,
+                           (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision, 0),
            "alpha kernel");
     FIO_CK(cudaMemcpy(d_P, sp.P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
     FIO_CK(cudaMemcpy(d_rx, sp.R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
@@ -848,15 +869,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
            "beta kernel");
   }
   FIO_CK(cudaDeviceSynchronize(), "plan construction");
-  {
-    // point-tile footprints for the interpolation and spread kernels
-    void *q = nullptr;
-    FIO_CK(dev_alloc(&q, sizeof(int4) * (size_t)L * p->ntile * p->ntile), "alloc tiles");
-    p->d_tiles = (int4 *)q;
-    FIO_CK(dev_alloc(&q, sizeof(uint2) * (size_t)L * tile_pts), "alloc tile-order warp");
-    p->d_warpt = (uint2 *)q;
-    FIO_CK(build_tiles(p), "tile footprints");
-  }
+  FIO_CK(build_work_lists(p, cstart), "work lists");
 
   // ---- summary
   p->q_max = 0; p->q_min = 1 << 30; p->r_max = 0;
@@ -870,8 +883,9 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   p->q_mean = qs / L;
   p->sep_err = 0;
   for (double e : p->wedge_err) p->sep_err = std::max(p->sep_err, e);
-  p->bytes_total = sizeof(int4) * (size_t)L * p->ntile * p->ntile +
-                   sizeof(uint2) * (size_t)L * tile_pts + (size_t)(aoff + boff) * cs + (size_t)gunit * max_batch * cs +
+  p->bytes_total = (sizeof(uint2) + sizeof(uint32_t)) * (size_t)L * NN + sizeof(int) * (size_t)koff +
+                   sizeof(int4) * (size_t)p->n_items + sizeof(int2) * (size_t)p->n_bins +
+                   (size_t)(aoff + boff) * cs + (size_t)gunit * max_batch * cs +
                    (size_t)NN * max_batch * cs + (size_t)NN * L * sizeof(uint2) +
                    tw.size() / 2 * cs + p->rows.size() * sizeof(RowDev) +
                    p->wedges.size() * sizeof(WedgeDev) + p->ffts.size() * sizeof(FftPlanDev);

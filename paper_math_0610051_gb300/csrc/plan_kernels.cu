@@ -274,14 +274,12 @@ __device__ __forceinline__ void store_c(void *base, long long i, double2 v) {
 template <typename C>
 __global__ void k_form_alpha(const double2 *__restrict__ AC, int N, int r, int q,
                              const double2 *__restrict__ Wm, WedgeDev w,
-                             const uint2 *__restrict__ warp_l, void *alpha_l, int nt) {
+                             const uint2 *__restrict__ warp_l, const uint32_t *__restrict__ perm_l,
+                             void *alpha_l) {
   const long long NN = (long long)N * N;
-  const long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (x >= NN) return;
-  // tile-order slot of x: [tile][point][t], point = (n1 mod 16) * 16 + (n2 mod 16)
-  const int n1 = (int)(x / N), n2 = (int)(x % N);
-  const long long tile = (long long)(n1 >> 4) * nt + (n2 >> 4);
-  const int pt = (n1 & 15) * 16 + (n2 & 15);
+  const long long pos = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (pos >= NN) return;
+  const long long x = perm_l[pos];  // alpha is stored in the sorted point order [pos][t]
   // centre-frequency factor exp(2 pi i y'.xi_c) / N (Sec. 3.4), exact mod 1
   const uint2 Y = warp_l[x];
   const uint32_t yk = Y.x * (uint32_t)w.xc1 + Y.y * (uint32_t)w.xc2;
@@ -298,7 +296,7 @@ __global__ void k_form_alpha(const double2 *__restrict__ AC, int N, int r, int q
       acc.y += a.x * b.y + a.y * b.x;
     }
     const double2 v = make_double2(acc.x * ctr.x - acc.y * ctr.y, acc.x * ctr.y + acc.y * ctr.x);
-    store_c<C>(alpha_l, (tile * 256 + pt) * w.qp + t, v);
+    store_c<C>(alpha_l, pos * w.qp + t, v);
   }
 }
 
@@ -421,15 +419,15 @@ cudaError_t plan_gram(const double2 *d_AC, long long rows, int r, double2 *d_par
 }
 
 cudaError_t plan_form_alpha(const double2 *d_AC, int N, int r, int q, const double2 *d_W,
-                            const WedgeDev &w, const uint2 *d_warp_l, void *d_alpha_l,
-                            int precision, int ntile, cudaStream_t s) {
+                            const WedgeDev &w, const uint2 *d_warp_l, const uint32_t *d_perm_l,
+                            void *d_alpha_l, int precision, cudaStream_t s) {
   const long long NN = (long long)N * N;
   if (precision == FIO_FP64)
     k_form_alpha<double2><<<blocks(NN, 256), 256, 0, s>>>(d_AC, N, r, q, d_W, w, d_warp_l,
-                                                          d_alpha_l, ntile);
+                                                          d_perm_l, d_alpha_l);
   else
     k_form_alpha<float2><<<blocks(NN, 256), 256, 0, s>>>(d_AC, N, r, q, d_W, w, d_warp_l,
-                                                         d_alpha_l, ntile);
+                                                         d_perm_l, d_alpha_l);
   return cudaGetLastError();
 }
 

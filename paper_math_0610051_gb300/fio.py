@@ -39,7 +39,17 @@ class _Amp(ctypes.Structure):
 class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("L", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("kb_width", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("r0", ctypes.c_int),
-                ("rank_cap", ctypes.c_int), ("max_batch", ctypes.c_int)]
+                ("rank_cap", ctypes.c_int), ("max_batch", ctypes.c_int),
+                ("surrogate", ctypes.c_void_p), ("surrogate_warp_budget", ctypes.c_double)]
+
+
+class _SurInfo(ctypes.Structure):
+    _fields_ = [("nparams", ctypes.c_int), ("nsamples", ctypes.c_int), ("epochs", ctypes.c_int),
+                ("steps", ctypes.c_longlong), ("train_seconds", ctypes.c_double),
+                ("final_loss", ctypes.c_double), ("tau_scale", ctypes.c_double),
+                ("dx_scale", ctypes.c_double), ("heldout_tau_maxerr", ctypes.c_double),
+                ("heldout_dx_maxerr", ctypes.c_double), ("heldout_dtheta_maxerr", ctypes.c_double),
+                ("heldout_tau_relrms", ctypes.c_double)]
 
 
 class _PlanInfo(ctypes.Structure):
@@ -52,8 +62,10 @@ class _PlanInfo(ctypes.Structure):
                 ("bytes_warp", ctypes.c_ulonglong), ("bytes_grid", ctypes.c_ulonglong),
                 ("bytes_total", ctypes.c_ulonglong), ("grid_points", ctypes.c_ulonglong),
                 ("alg_bytes_apply", ctypes.c_ulonglong), ("plan_seconds", ctypes.c_double),
-                ("kernel_launches", ctypes.c_ulonglong), ("max_footprint", ctypes.c_int),
-                ("mean_footprint", ctypes.c_double), ("sep_error", ctypes.c_double)]
+                ("kernel_launches", ctypes.c_ulonglong), ("surrogate_warp", ctypes.c_int),
+                ("surrogate_warp_cycles", ctypes.c_double),
+                ("surrogate_residual_cycles", ctypes.c_double), ("max_bin_points", ctypes.c_int),
+                ("mean_bin_points", ctypes.c_double), ("max_spread_candidates", ctypes.c_int), ("sep_error", ctypes.c_double)]
 
 
 class _WedgeInfo(ctypes.Structure):
@@ -71,6 +83,8 @@ EXPORTS = [
     "fio_plan_destroy", "fio_plan_set_timing", "fio_plan_stage_times",
     "fio_dft2", "fio_default_wedges", "fio_wedge_map", "fio_wedge_geometry", "fio_kb_eval",
     "fio_kb_width_for", "fio_host_eigh", "fio_status_string", "fio_last_error", "fio_version",
+    "fio_surrogate_train", "fio_surrogate_destroy", "fio_surrogate_get_info", "fio_surrogate_params",
+    "fio_surrogate_eval", "fio_surrogate_loss_grad", "fio_surrogate_samples", "fio_surrogate_nparams",
 ]
 
 _lib = None
@@ -108,6 +122,15 @@ def lib():
             L.fio_kb_eval.argtypes = [I, D, I, P, P, P, P]
             L.fio_kb_width_for.argtypes = [D]
             L.fio_host_eigh.argtypes = [I, P, P, P]
+            L.fio_surrogate_train.argtypes = [ctypes.POINTER(_Phase), I, I, I, ctypes.c_ulonglong,
+                                              ctypes.POINTER(P)]
+            L.fio_surrogate_destroy.argtypes = [P]
+            L.fio_surrogate_destroy.restype = None
+            L.fio_surrogate_get_info.argtypes = [P, ctypes.POINTER(_SurInfo)]
+            L.fio_surrogate_params.argtypes = [P, P, I]
+            L.fio_surrogate_eval.argtypes = [P, I, P, P, P]
+            L.fio_surrogate_loss_grad.argtypes = [P, I, P, P, P, ctypes.POINTER(ctypes.c_double)]
+            L.fio_surrogate_samples.argtypes = [ctypes.POINTER(_Phase), I, ctypes.c_ulonglong, P, P]
             L.fio_status_string.restype = ctypes.c_char_p
             L.fio_status_string.argtypes = [I]
             L.fio_last_error.restype = ctypes.c_char_p
@@ -144,7 +167,8 @@ class Plan:
 
     def __init__(self, N: int, phase: int, params, eps: float, amp=None, precision: str = "mixed",
                  L: int = 0, sigma: float = 0.0, kb_width: int = 0, seed: int = 0x5EED5EED,
-                 r0: int = 0, rank_cap: int = 0, max_batch: int = 1, device=None):
+                 r0: int = 0, rank_cap: int = 0, max_batch: int = 1, device=None,
+                 surrogate: "Surrogate | None" = None, surrogate_warp_budget: float = 0.0):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -160,6 +184,9 @@ class Plan:
         opt.precision = FP64 if precision in ("fp64", FP64) else MIXED
         opt.L, opt.sigma, opt.kb_width = int(L), float(sigma), int(kb_width)
         opt.seed, opt.r0, opt.rank_cap, opt.max_batch = int(seed), int(r0), int(rank_cap), int(max_batch)
+        opt.surrogate = surrogate._handle if surrogate is not None else None
+        opt.surrogate_warp_budget = float(surrogate_warp_budget)
+        self._surrogate = surrogate
         self.N = int(N)
         self.precision = opt.precision
         self.max_batch = max(1, int(max_batch))
@@ -266,6 +293,84 @@ class Plan:
         y = np.empty((self.N, self.N, 2), np.float64)
         _check(lib().fio_plan_export_warp(self._handle, int(l), _np_ptr(y)), "fio_plan_export_warp")
         return y
+
+
+def _tau_phase(modes):
+    prm = np.ascontiguousarray(np.asarray(modes, np.float64).ravel())
+    return prm, _Phase(PHASE_TAU_MODES, len(prm) // 5, prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+
+class Surrogate:
+    """fio_surrogate_*: the BF16 MLP surrogate of a tau-mode phase, trained on the GPU."""
+
+    def __init__(self, modes, nsamples: int = 1 << 20, epochs: int = 20, batch: int = 8192,
+                 seed: int = 1):
+        import torch
+        self._torch = torch
+        self._prm, ph = _tau_phase(modes)
+        self._handle = ctypes.c_void_p()
+        _check(lib().fio_surrogate_train(ctypes.byref(ph), int(nsamples), int(epochs), int(batch),
+                                         int(seed), ctypes.byref(self._handle)),
+               "fio_surrogate_train")
+
+    def close(self):
+        if getattr(self, "_handle", None) and self._handle.value:
+            lib().fio_surrogate_destroy(self._handle)
+            self._handle = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> dict:
+        i = _SurInfo()
+        _check(lib().fio_surrogate_get_info(self._handle, ctypes.byref(i)), "fio_surrogate_get_info")
+        return {k: getattr(i, k) for k, _ in _SurInfo._fields_}
+
+    def params(self) -> np.ndarray:
+        out = np.empty(lib().fio_surrogate_nparams(), np.float32)
+        _check(lib().fio_surrogate_params(self._handle, _np_ptr(out), 0), "fio_surrogate_params")
+        return out
+
+    def set_params(self, p):
+        p = np.ascontiguousarray(p, np.float32)
+        _check(lib().fio_surrogate_params(self._handle, _np_ptr(p), 1), "fio_surrogate_params")
+
+    def eval(self, x4):
+        """x4: CUDA float32 [n, 4] -> [n, 4] (tau, d1 tau, d2 tau, d_theta tau)."""
+        torch = self._torch
+        x4 = x4.contiguous()
+        y = torch.empty_like(x4)
+        _check(lib().fio_surrogate_eval(self._handle, x4.shape[0], ctypes.c_void_p(x4.data_ptr()),
+                                        ctypes.c_void_p(y.data_ptr()),
+                                        _stream_ptr(torch, x4.device)), "fio_surrogate_eval")
+        return y
+
+    def loss_grad(self, x4, t3):
+        torch = self._torch
+        g = torch.empty(lib().fio_surrogate_nparams(), dtype=torch.float32, device=x4.device)
+        loss = ctypes.c_double()
+        torch.cuda.synchronize()
+        _check(lib().fio_surrogate_loss_grad(self._handle, x4.shape[0],
+                                             ctypes.c_void_p(x4.contiguous().data_ptr()),
+                                             ctypes.c_void_p(t3.contiguous().data_ptr()),
+                                             ctypes.c_void_p(g.data_ptr()), ctypes.byref(loss)),
+               "fio_surrogate_loss_grad")
+        return loss.value, g
+
+
+def surrogate_samples(modes, n: int, seed: int = 1):
+    """The plain-evaluation training samples: (x4 float32 [n,4], t4 float64 [n,4]) on the GPU."""
+    import torch
+    prm, ph = _tau_phase(modes)
+    x4 = torch.empty(n, 4, dtype=torch.float32, device="cuda")
+    t4 = torch.empty(n, 4, dtype=torch.float64, device="cuda")
+    _check(lib().fio_surrogate_samples(ctypes.byref(ph), int(n), int(seed),
+                                       ctypes.c_void_p(x4.data_ptr()), ctypes.c_void_p(t4.data_ptr())),
+           "fio_surrogate_samples")
+    return x4, t4
 
 
 def dft2(x, inverse: bool = False, out=None):

@@ -149,9 +149,14 @@ def test_tau_modes_amplitude_batch(env, orc):
         x = dev(torch, f, "mixed")
         out = plan.apply(x).cpu().numpy()
         one = plan.apply(x[5:6].clone()).cpu().numpy()
-        plan.adjoint(x)
+        adj = plan.adjoint(x).cpu().numpy()
+        adj_one = plan.adjoint(x[5:6].clone()).cpu().numpy()
         plan.sync()
-    assert np.array_equal(one[0], out[5])  # batching does not change the arithmetic
+    # Batching does not change the arithmetic. The forward sum over wedges is an
+    # atomic add, so its order (and the last float32 bit) may differ between runs;
+    # the adjoint has no atomics and is bit-identical.
+    assert rel(out[5], one[0]) < 1e-6
+    assert np.array_equal(adj_one[0], adj[5])
     ph, amp = orc.Phase(orc.TAU_MODES, prm), orc.Amplitude(1, 0.5, 0.3)
     n1, n2 = synth.sample_points(N, 256, seed=2)
     for b in (0, 7):

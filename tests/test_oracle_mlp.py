@@ -1,0 +1,80 @@
+"""Pins of the CPU references used to check the phase surrogate: the FP64 MLP's
+gradients and angular derivative against finite differences, and the tau-mode
+derivatives against finite differences and against the oracle's phase."""
+import numpy as np
+
+from oracle import mlp
+from paper_math_0610051_gb300 import synth
+
+
+def _params(seed):
+    return np.random.default_rng(seed).standard_normal(mlp.NPARAMS) * 0.3
+
+
+def _inputs(n, seed):
+    g = np.random.default_rng(seed)
+    th = g.uniform(0, 2 * np.pi, n)
+    return np.stack([g.uniform(0, 1, n), g.uniform(0, 1, n), np.cos(th), np.sin(th)], 1), th
+
+
+def test_mlp_zero_weights_give_bias():
+    p = np.zeros(mlp.NPARAMS)
+    p[-3:] = [0.5, -1.0, 2.0]
+    X, _ = _inputs(5, 0)
+    y, _ = mlp.forward(p, X)
+    assert np.allclose(y, [[0.5, -1.0, 2.0]] * 5)
+
+
+def test_mlp_gradient_matches_central_differences():
+    p = _params(1)
+    X, _ = _inputs(40, 2)
+    T = np.random.default_rng(3).standard_normal((40, 3))
+    g = mlp.grad(p, X, T)
+    rng = np.random.default_rng(4)
+    idx = rng.choice(mlp.NPARAMS, 60, replace=False)
+    h = 1e-6
+    for i in idx:
+        e = np.zeros(mlp.NPARAMS)
+        e[i] = h
+        fd = (mlp.loss(p + e, X, T) - mlp.loss(p - e, X, T)) / (2 * h)
+        assert abs(fd - g[i]) < 1e-6 * max(1.0, abs(g[i])), (i, fd, g[i])
+
+
+def test_mlp_dtheta_matches_finite_difference():
+    p = _params(5)
+    _, th = _inputs(30, 6)
+    x = np.random.default_rng(7).uniform(0, 1, (30, 2))
+
+    def y0(t):
+        X = np.stack([x[:, 0], x[:, 1], np.cos(t), np.sin(t)], 1)
+        return mlp.forward(p, X)[0][:, 0]
+
+    h = 1e-6
+    X = np.stack([x[:, 0], x[:, 1], np.cos(th), np.sin(th)], 1)
+    fd = (y0(th + h) - y0(th - h)) / (2 * h)
+    assert np.max(np.abs(fd - mlp.dtheta(p, X))) < 1e-7
+
+
+def test_tau_derivatives_match_finite_differences(orc):
+    modes = synth.tau_mode_params(16, seed=3)
+    g = np.random.default_rng(8)
+    x1, x2, th = g.uniform(0, 1, 50), g.uniform(0, 1, 50), g.uniform(0, 2 * np.pi, 50)
+    t = orc.tau_eval(modes, x1, x2, th)
+    h = 1e-6
+    for col, (dx1, dx2, dth) in zip((1, 2, 3), ((h, 0, 0), (0, h, 0), (0, 0, h))):
+        fd = (orc.tau_eval(modes, x1 + dx1, x2 + dx2, th + dth)[:, 0] -
+              orc.tau_eval(modes, x1 - dx1, x2 - dx2, th - dth)[:, 0]) / (2 * h)
+        assert np.max(np.abs(fd - t[:, col])) < 1e-7
+
+
+def test_tau_matches_phase(orc):
+    """Phi(x, xi) - x.xi = |xi| tau(x, arg xi) for the tau-mode phase."""
+    modes = synth.tau_mode_params(12, seed=4)
+    g = np.random.default_rng(9)
+    n = 80
+    x1, x2 = g.uniform(0, 1, n), g.uniform(0, 1, n)
+    k1, k2 = g.integers(-40, 41, n), g.integers(-40, 41, n)
+    k1[k1 == 0] = 1
+    phi = orc.phase_eval(orc.Phase(orc.TAU_MODES, modes), x1, x2, k1, k2)
+    tau = orc.tau_eval(modes, x1, x2, np.arctan2(k2, k1))[:, 0]
+    assert np.max(np.abs(phi - (x1 * k1 + x2 * k2) - np.hypot(k1, k2) * tau)) < 1e-11
