@@ -31,7 +31,8 @@ METRIC = "FIO outputs/s at N=1024, rel-L2<=1e-4 (mixed vs FP64 path), % HBM roof
 UNIT = "outputs/s"
 FALLBACK_HBM_GBS = 6800.0
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
-KERNEL_SRC = os.path.join(ROOT, "paper_math_0610051_gb300", "csrc", "apply.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_math_0610051_gb300", "csrc", f)
+               for f in ("interp.cu", "apply.cu", "apply_common.cuh", "fft_engine.cuh")]
 
 
 def log(*a):
@@ -96,8 +97,13 @@ def peaks():
 
 
 def kernel_sha():
-    with open(KERNEL_SRC, "rb") as fh:
-        return hashlib.sha256(fh.read()).hexdigest()[:16]
+    """Hash of the apply-path kernel sources: a recorded traffic figure is used
+    only while these are unchanged since its capture."""
+    h = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        with open(f, "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel, batch, N):
@@ -314,7 +320,7 @@ def run_ours(a, world, rank, local):
     per_launch_s = top_ms / max(top_cnt, 1) / 1e3
     achieved = sb[top] / per_launch_s / 1e9
     peak, peak_kind = peaks()
-    kname = {"S3_interp": "k_interp", "S4a_spread": "k_spread"}.get(top, top)
+    kname = {"S3_interp": "k_interp_bin", "S4a_spread": "k_spread_bin"}.get(top, top)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": recorded_traffic(kname, B, N),
                 "kernel": top, "peak_source": peak_kind,

@@ -28,6 +28,19 @@
 
 namespace fio {
 
+// Lines per CTA of an in-place line FFT of length n (S1, S2, S4b): the CTA's
+// buffer holds 8192 complex64 or 4096 complex128 values (64 KB), and a line
+// transfer is at most 32 elements wide.
+__host__ __device__ inline int fft_lines(int n, int prec) {
+  const int elems = prec == FIO_FP64 ? 4096 : 8192;
+  const int nl = elems / n;
+  return nl < 1 ? 1 : (nl > 32 ? 32 : nl);
+}
+constexpr int kFftThreads = 512;  // threads of the in-place line-FFT kernels
+template <typename T> __host__ __device__ constexpr int prec_of() {
+  return sizeof(T) == 4 ? FIO_MIXED : FIO_FP64;
+}
+
 // --------------------------------------------------------------- S0 / S4d --
 // Unitary 2D DFT passes.  Rows: lines are rows of N contiguous elements.
 // load index (e + load_shift) mod N, store index (e + store_shift) mod N.
@@ -54,8 +67,9 @@ k_dft_rows(const Cx<T> *in, Cx<T> *out, int N, int nrows, int nl, int sign, int 
   }
   for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
     const int e = it % N, l = it / N;
-    a[e * nlc + l] = in[(size_t)(r0 + l) * N + (e + load_shift) % N];
+    cp_async_elem(&a[e * nlc + l], &in[(size_t)(r0 + l) * N + (e + load_shift) % N]);
   }
+  cp_async_wait();
   __syncthreads();
   C *res = fft_exec(a, b, N, nlc, pl, sign, tw);
   for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
@@ -91,8 +105,9 @@ k_dft_cols(const Cx<T> *in, Cx<T> *out, int N, int nl, int sign, int load_shift,
   }
   for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
     const int l = it % nlc, e = it / nlc;
-    a[e * nlc + l] = in[base + (size_t)((e + load_shift) % N) * N + l];
+    cp_async_elem(&a[e * nlc + l], &in[base + (size_t)((e + load_shift) % N) * N + l]);
   }
+  cp_async_wait();
   __syncthreads();
   C *res = fft_exec(a, b, N, nlc, pl, sign, tw);
   for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
@@ -102,66 +117,69 @@ k_dft_cols(const Cx<T> *in, Cx<T> *out, int N, int nl, int sign, int load_shift,
 }
 
 // ----------------------------------------------------------------- S1 ------
-// One CTA per (box row, chunk of nl channels): scatter beta' fhat into the
-// zero-padded row and FFT it along g2 with exp(+2 pi i).
+// One CTA per (box row, chunk of fft_lines(m2) channels): scatter beta' fhat into
+// the zero-padded row and FFT it along g2 with exp(+2 pi i), in place.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFftThreads)
 k_scatter_rowfft(const Cx<T> *__restrict__ fhat, const WedgeDev *__restrict__ W,
                  const RowDev *__restrict__ rows, const FftPlanDev *__restrict__ ffts,
                  const Cx<T> *__restrict__ tw_all, const Cx<T> *__restrict__ beta,
-                 Cx<T> *__restrict__ grid, int N, int B, int nl) {
+                 Cx<T> *__restrict__ grid, int N, int B) {
   using C = Cx<T>;
   extern __shared__ unsigned char smem_raw[];
   const RowDev rw = rows[blockIdx.x];
   const WedgeDev w = W[rw.wedge];
   const int nch = B * w.qp;
+  const int n = w.m2;
+  const int nl = fft_lines(n, prec_of<T>());
   const int c0 = blockIdx.y * nl;
   if (c0 >= nch) return;
   const int nlc = min(nl, nch - c0);
-  const int n = w.m2;
   C *a = reinterpret_cast<C *>(smem_raw);
-  C *b = a + n * nl;
-  C *tw = b + n * nl;
+  C *tw = a + n * nl;
   for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw2_off + k];
   for (int k = threadIdx.x; k < n * nlc; k += blockDim.x) a[k] = C{0, 0};
   __syncthreads();
   const int k1pp = rw.xi1 + w.xc1;
-  for (int it = threadIdx.x; it < rw.len * nlc; it += blockDim.x) {
-    const int l = it % nlc, j = it / nlc;
-    const int ch = c0 + l, bb = ch / w.qp, t = ch - bb * w.qp;
-    const int x2p = rw.a + j;
-    const int k2pp = x2p + w.xc2;
-    const int k1 = w.Minv[0] * k1pp + w.Minv[1] * k2pp;
-    const int k2 = w.Minv[2] * k1pp + w.Minv[3] * k2pp;
-    const size_t idx = (size_t)imodp(k1, N) * N + imodp(k2, N);
-    const C v = cmul(beta[w.beta_off + (long long)t * w.npts + rw.pt + j],
-                     fhat[(size_t)bb * N * N + idx]);
-    a[imodp(x2p, n) * nlc + l] = v;
+  const LineMap lm = line_map(nlc);
+  if ((int)threadIdx.x < lm.lanes) {
+    const int ch = c0 + lm.l, bb = ch / w.qp, t = ch - bb * w.qp;
+    const C *bt = beta + w.beta_off + (long long)t * w.npts + rw.pt;
+    const C *fb = fhat + (size_t)bb * N * N;
+    for (int j = lm.i0; j < rw.len; j += lm.step) {
+      const int x2p = rw.a + j;
+      const int k2pp = x2p + w.xc2;
+      const int k1 = w.Minv[0] * k1pp + w.Minv[1] * k2pp;
+      const int k2 = w.Minv[2] * k1pp + w.Minv[3] * k2pp;
+      const size_t idx = (size_t)imodp(k1, N) * N + imodp(k2, N);
+      a[imodp(x2p, n) * nlc + lm.l] = cmul(bt[j], fb[idx]);
+    }
   }
   __syncthreads();
-  const C *res = fft_exec(a, b, n, nlc, ffts[w.fft2], +1, tw);
+  const FftPlanDev pl = ffts[w.fft2];
+  fft_exec_dif(a, n, nlc, pl, +1, tw);
   C *out = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * n * nch + c0;
-  for (int it = threadIdx.x; it < n * nlc; it += blockDim.x) {
-    const int l = it % nlc, e = it / nlc;
-    out[(long long)e * nch + l] = res[e * nlc + l];
-  }
+  if ((int)threadIdx.x < lm.lanes)
+    for (int e = lm.i0; e < n; e += lm.step)
+      out[(long long)e * nch + lm.l] = a[fft_dif_pos(e, pl) * nlc + lm.l];
 }
 
 // ------------------------------------------------------------ S2 / S4b -----
-// Column FFTs along g1.  A CTA owns nl consecutive entries of the flattened
-// [g2][ch] dimension of one wedge.  adjoint = 0: input rows outside the box
-// are zero (not read), all m1 outputs written, exp(+2 pi i).  adjoint = 1:
-// all rows read, only box rows written, exp(-2 pi i).
+// Column FFTs along g1, in place.  A CTA owns fft_lines(m1) consecutive entries
+// of the flattened [g2][ch] dimension of one wedge.  adjoint = 0: input rows
+// outside the box are zero (not read), all m1 outputs written, exp(+2 pi i).
+// adjoint = 1: all rows read, only box rows written, exp(-2 pi i).
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFftThreads)
 k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
          const FftPlanDev *__restrict__ ffts, const Cx<T> *__restrict__ tw_all, int L, int B,
-         int nl, int adjoint) {
+         int adjoint) {
   using C = Cx<T>;
   extern __shared__ unsigned char smem_raw[];
   // locate (wedge, chunk) for this block
-  int blk = blockIdx.x, l = 0;
+  int blk = blockIdx.x, l = 0, nl = 1;
   for (; l < L; ++l) {
+    nl = fft_lines(W[l].m1, prec_of<T>());
     const int cnt = (W[l].m2 * B * W[l].qp + nl - 1) / nl;
     if (blk < cnt) break;
     blk -= cnt;
@@ -174,73 +192,74 @@ k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   const int nlc = (int)min((long long)nl, rs - cc0);
   const int n = w.m1;
   C *a = reinterpret_cast<C *>(smem_raw);
-  C *b = a + n * nl;
-  C *tw = b + n * nl;
+  C *tw = a + n * nl;
   C *g = grid + w.grid_unit * B + cc0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw1_off + k];
+  const LineMap lm = line_map(nlc);
+  const bool on = (int)threadIdx.x < lm.lanes;
+  const int c = lm.l;
   if (!adjoint) {
     for (int k = threadIdx.x; k < n * nlc; k += blockDim.x) a[k] = C{0, 0};
     __syncthreads();
-    for (int it = threadIdx.x; it < w.n1 * nlc; it += blockDim.x) {
-      const int c = it % nlc, e = it / nlc;
-      const int g1 = imodp(w.b1 + e, n);
-      a[g1 * nlc + c] = g[g1 * rs + c];
-    }
-  } else {
-    for (int it = threadIdx.x; it < n * nlc; it += blockDim.x) {
-      const int c = it % nlc, e = it / nlc;
-      a[e * nlc + c] = g[e * rs + c];
-    }
+    if (on)
+      for (int e = lm.i0; e < w.n1; e += lm.step) {
+        const int g1 = imodp(w.b1 + e, n);
+        cp_async_elem(&a[g1 * nlc + c], &g[g1 * rs + c]);
+      }
+  } else if (on) {
+    for (int e = lm.i0; e < n; e += lm.step) cp_async_elem(&a[e * nlc + c], &g[e * rs + c]);
   }
+  cp_async_wait();
   __syncthreads();
-  const C *res = fft_exec(a, b, n, nlc, ffts[w.fft1], adjoint ? -1 : +1, tw);
+  const FftPlanDev pl = ffts[w.fft1];
+  fft_exec_dif(a, n, nlc, pl, adjoint ? -1 : +1, tw);
+  if (!on) return;
   if (!adjoint) {
-    for (int it = threadIdx.x; it < n * nlc; it += blockDim.x) {
-      const int c = it % nlc, e = it / nlc;
-      g[e * rs + c] = res[e * nlc + c];
-    }
+    for (int e = lm.i0; e < n; e += lm.step) g[e * rs + c] = a[fft_dif_pos(e, pl) * nlc + c];
   } else {
-    for (int it = threadIdx.x; it < w.n1 * nlc; it += blockDim.x) {
-      const int c = it % nlc, e = it / nlc;
+    for (int e = lm.i0; e < w.n1; e += lm.step) {
       const int g1 = imodp(w.b1 + e, n);
-      g[g1 * rs + c] = res[g1 * nlc + c];
+      g[g1 * rs + c] = a[fft_dif_pos(g1, pl) * nlc + c];
     }
   }
 }
 
 // ---------------------------------------------------------------- S4b rows --
-// Row FFT along g2 with exp(-2 pi i) for each box row; only the run's
-// columns are written back.
+// Row FFT along g2 with exp(-2 pi i) for each box row, in place; only the
+// run's columns are written back.
 template <typename T>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kFftThreads)
 k_rowfft_adj(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
              const RowDev *__restrict__ rows, const FftPlanDev *__restrict__ ffts,
-             const Cx<T> *__restrict__ tw_all, int B, int nl) {
+             const Cx<T> *__restrict__ tw_all, int B) {
   using C = Cx<T>;
   extern __shared__ unsigned char smem_raw[];
   const RowDev rw = rows[blockIdx.x];
   const WedgeDev w = W[rw.wedge];
   const int nch = B * w.qp;
+  const int n = w.m2;
+  const int nl = fft_lines(n, prec_of<T>());
   const int c0 = blockIdx.y * nl;
   if (c0 >= nch || rw.len == 0) return;
   const int nlc = min(nl, nch - c0);
-  const int n = w.m2;
   C *a = reinterpret_cast<C *>(smem_raw);
-  C *b = a + n * nl;
-  C *tw = b + n * nl;
+  C *tw = a + n * nl;
   C *row = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * n * nch + c0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw2_off + k];
-  for (int it = threadIdx.x; it < n * nlc; it += blockDim.x) {
-    const int l = it % nlc, e = it / nlc;
-    a[e * nlc + l] = row[(long long)e * nch + l];
-  }
+  const LineMap lm = line_map(nlc);
+  const bool on = (int)threadIdx.x < lm.lanes;
+  if (on)
+    for (int e = lm.i0; e < n; e += lm.step)
+      cp_async_elem(&a[e * nlc + lm.l], &row[(long long)e * nch + lm.l]);
+  cp_async_wait();
   __syncthreads();
-  const C *res = fft_exec(a, b, n, nlc, ffts[w.fft2], -1, tw);
-  for (int it = threadIdx.x; it < rw.len * nlc; it += blockDim.x) {
-    const int l = it % nlc, j = it / nlc;
-    const int g2 = imodp(rw.a + j, n);
-    row[(long long)g2 * nch + l] = res[g2 * nlc + l];
-  }
+  const FftPlanDev pl = ffts[w.fft2];
+  fft_exec_dif(a, n, nlc, pl, -1, tw);
+  if (on)
+    for (int j = lm.i0; j < rw.len; j += lm.step) {
+      const int g2 = imodp(rw.a + j, n);
+      row[(long long)g2 * nch + lm.l] = a[fft_dif_pos(g2, pl) * nlc + lm.l];
+    }
 }
 
 // ---------------------------------------------------------------- S4c ------
@@ -322,16 +341,25 @@ cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int bat
 
 
 struct LaunchGeom {
-  int max_m1 = 0, max_m2 = 0, max_q = 0, col_blocks = 0;
+  int max_m1 = 0, max_m2 = 0, max_q = 0, col_blocks = 0, row_chunks = 0;
+  size_t smem_col = 0, smem_row = 0;
 };
 
-static LaunchGeom geom(const fio_plan_s *p, int B, int nl_col) {
+// Launch shapes of the in-place line FFTs: column blocks, row-chunk count and
+// the largest shared buffers (n * fft_lines(n) + n twiddles).
+static LaunchGeom geom(const fio_plan_s *p, int B) {
   LaunchGeom g;
+  const int prec = p->precision;
+  const size_t cs = prec == FIO_FP64 ? 16 : 8;
   for (const auto &w : p->wedges) {
     g.max_m1 = std::max(g.max_m1, w.m1);
     g.max_m2 = std::max(g.max_m2, w.m2);
     g.max_q = std::max(g.max_q, w.qp);
-    g.col_blocks += (w.m2 * B * w.qp + nl_col - 1) / nl_col;
+    const int nl1 = fft_lines(w.m1, prec), nl2 = fft_lines(w.m2, prec);
+    g.col_blocks += (w.m2 * B * w.qp + nl1 - 1) / nl1;
+    g.row_chunks = std::max(g.row_chunks, (B * w.qp + nl2 - 1) / nl2);
+    g.smem_col = std::max(g.smem_col, ((size_t)w.m1 * nl1 + w.m1) * cs);
+    g.smem_row = std::max(g.smem_row, ((size_t)w.m2 * nl2 + w.m2) * cs);
   }
   return g;
 }
@@ -383,9 +411,7 @@ template <typename T>
 static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int B,
                               cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing) {
   using C = Cx<T>;
-  const int prec = p->precision;
   const int N = p->N, L = p->L;
-  const long long NN = (long long)N * N;
   const void *twN;
   const FftPlanDev plN = plan_for_N(p, &twN);
   cudaError_t e;
@@ -396,28 +422,23 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
     p->launches += 2;
   }
   if (e != cudaSuccess) return e;
-  const LaunchGeom g0 = geom(p, B, 1);
+  const LaunchGeom g0 = geom(p, B);
   // S1
-  const int nl1 = pick_nl(g0.max_m2, prec, 16);
-  const size_t sm1 = apply_smem_bytes(g0.max_m2, nl1, prec);
-  if ((e = set_smem(k_scatter_rowfft<T>, sm1)) != cudaSuccess) return e;
-  dim3 g1((unsigned)p->rows.size(), (unsigned)((B * g0.max_q + nl1 - 1) / nl1));
+  if ((e = set_smem(k_scatter_rowfft<T>, g0.smem_row)) != cudaSuccess) return e;
   {
     StageTimer st(p, s, FIO_STAGE_S1_SCATTER, timing);
-    k_scatter_rowfft<T><<<g1, kThreads, sm1, s>>>((const C *)fhat_ws, p->d_wedges, p->d_rows,
-                                                  p->d_ffts, (const C *)p->d_twiddle,
-                                                  (const C *)p->d_beta, (C *)grid_ws, N, B, nl1);
+    k_scatter_rowfft<T><<<dim3((unsigned)p->rows.size(), (unsigned)g0.row_chunks), kFftThreads,
+                          g0.smem_row, s>>>((const C *)fhat_ws, p->d_wedges, p->d_rows, p->d_ffts,
+                                            (const C *)p->d_twiddle, (const C *)p->d_beta,
+                                            (C *)grid_ws, N, B);
     p->launches += 1;
   }
   // S2
-  const int nl2 = pick_nl(g0.max_m1, prec, 16);
-  const size_t sm2 = apply_smem_bytes(g0.max_m1, nl2, prec);
-  if ((e = set_smem(k_colfft<T>, sm2)) != cudaSuccess) return e;
-  const LaunchGeom g2 = geom(p, B, nl2);
+  if ((e = set_smem(k_colfft<T>, g0.smem_col)) != cudaSuccess) return e;
   {
     StageTimer st(p, s, FIO_STAGE_S2_COLFFT, timing);
-    k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)grid_ws, p->d_wedges, p->d_ffts,
-                                                     (const C *)p->d_twiddle, L, B, nl2, 0);
+    k_colfft<T><<<g0.col_blocks, kFftThreads, g0.smem_col, s>>>((C *)grid_ws, p->d_wedges, p->d_ffts,
+                                                            (const C *)p->d_twiddle, L, B, 0);
     p->launches += 1;
   }
   // S3
@@ -434,11 +455,8 @@ template <typename T>
 static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out, int B,
                                 cudaStream_t s) {
   using C = Cx<T>;
-  const int prec = p->precision;
   const int N = p->N, L = p->L;
-  const long long NN = (long long)N * N;
   cudaError_t e;
-  const size_t cs = prec == FIO_FP64 ? 16 : 8;
   // S4a (writes every grid cell)
   {
     StageTimer st(p, s, FIO_STAGE_S4A_SPREAD);
@@ -447,26 +465,22 @@ static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out,
     p->launches += 1;
   }
   // S4b columns
-  const LaunchGeom g0 = geom(p, B, 1);
-  const int nl2 = pick_nl(g0.max_m1, prec, 16);
-  const size_t sm2 = apply_smem_bytes(g0.max_m1, nl2, prec);
-  if ((e = set_smem(k_colfft<T>, sm2)) != cudaSuccess) return e;
-  const LaunchGeom g2 = geom(p, B, nl2);
+  const LaunchGeom g0 = geom(p, B);
+  if ((e = set_smem(k_colfft<T>, g0.smem_col)) != cudaSuccess) return e;
   {
     StageTimer st(p, s, FIO_STAGE_S4B_COLFFT);
-    k_colfft<T><<<g2.col_blocks, kThreads, sm2, s>>>((C *)p->d_grid, p->d_wedges, p->d_ffts,
-                                                     (const C *)p->d_twiddle, L, B, nl2, 1);
+    k_colfft<T><<<g0.col_blocks, kFftThreads, g0.smem_col, s>>>((C *)p->d_grid, p->d_wedges,
+                                                            p->d_ffts, (const C *)p->d_twiddle,
+                                                            L, B, 1);
     p->launches += 1;
   }
   // S4b rows
-  const int nl1 = pick_nl(g0.max_m2, prec, 16);
-  const size_t sm1 = apply_smem_bytes(g0.max_m2, nl1, prec);
-  if ((e = set_smem(k_rowfft_adj<T>, sm1)) != cudaSuccess) return e;
-  dim3 g1((unsigned)p->rows.size(), (unsigned)((B * g0.max_q + nl1 - 1) / nl1));
+  if ((e = set_smem(k_rowfft_adj<T>, g0.smem_row)) != cudaSuccess) return e;
   {
     StageTimer st(p, s, FIO_STAGE_S4B_ROWFFT);
-    k_rowfft_adj<T><<<g1, kThreads, sm1, s>>>((C *)p->d_grid, p->d_wedges, p->d_rows, p->d_ffts,
-                                              (const C *)p->d_twiddle, B, nl1);
+    k_rowfft_adj<T><<<dim3((unsigned)p->rows.size(), (unsigned)g0.row_chunks), kFftThreads,
+                      g0.smem_row, s>>>((C *)p->d_grid, p->d_wedges, p->d_rows, p->d_ffts,
+                                        (const C *)p->d_twiddle, B);
     p->launches += 1;
   }
   // S4c

@@ -22,6 +22,29 @@ __device__ __forceinline__ int imodp(int a, int n) {
 
 constexpr int kThreads = 256;
 
+// ------------------------------------------------ asynchronous staging -----
+// cp.async copies global -> shared without passing through registers, so a
+// thread can have all of its staging loads in flight at once.  Both addresses
+// must be aligned to the copy size.  cp_async_wait() waits for this thread's
+// copies; a barrier then makes every thread's copies visible.
+template <int BYTES>
+__device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+  if constexpr (BYTES == 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;\n" ::"r"(s), "l"(gmem), "n"(BYTES)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+// One complex element (8 or 16 bytes).
+template <typename C>
+__device__ __forceinline__ void cp_async_elem(C *smem, const C *gmem) {
+  cp_async<(int)sizeof(C)>(smem, gmem);
+}
+
 // ------------------------------------------------------------ KB kernel ----
 // phi(s) = I0(beta sqrt(1 - (2s/w)^2)) / I0(beta) for |s| < w/2, else 0.
 __device__ __forceinline__ float kb_phi(float s, float two_over_w, float beta, float inv_i0b) {

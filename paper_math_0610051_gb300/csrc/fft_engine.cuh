@@ -167,4 +167,112 @@ __device__ C *fft_exec(C *a, C *b, int n, int nl, const FftPlanDev &pl, int sign
   return a;
 }
 
+// ------------------------------------------------------- in-place variant --
+// Division by a runtime divisor d <= 4096 for x < 2^20: q = (x ceil(2^40 / d)) >> 40
+// is exact (the rounding error x (ceil(2^40/d) d - 2^40) / 2^40 stays below 1).
+struct FastDiv {
+  unsigned d;
+  unsigned long long M;
+};
+__host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
+  return FastDiv{d, ((1ULL << 40) + d - 1) / d};
+}
+__device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv &f) {
+  return (unsigned)(((unsigned long long)x * f.M) >> 40);
+}
+// x / R for the radices 2, 3, 4, 5, 8 and x < 2^16 (multiply-shift constants
+// ceil(2^17 / 3) and ceil(2^18 / 5), exact on that range).
+__device__ __forceinline__ int div_radix(int x, int R) {
+  switch (R) {
+    case 2: return x >> 1;
+    case 4: return x >> 2;
+    case 8: return x >> 3;
+    case 3: return (int)(((unsigned)x * 43691u) >> 17);
+    default: return (int)(((unsigned)x * 52429u) >> 18);
+  }
+}
+
+// The lines of an in-place transform are shared out with a fixed line per
+// thread: thread t < lanes works on line t % nl, items t / nl, t / nl + step, ...
+struct LineMap {
+  int lanes, l, i0, step;
+};
+__device__ __forceinline__ LineMap line_map(int nl) {
+  LineMap m;
+  m.step = blockDim.x / nl;
+  m.lanes = m.step * nl;
+  m.i0 = threadIdx.x / nl;
+  m.l = threadIdx.x - m.i0 * nl;
+  return m;
+}
+
+// Decimation in frequency on a single shared buffer.  A stage on blocks of
+// length m with radix R takes, for j < m/R, x_r = a[j + r m/R] (r < R), forms
+// X_k = sum_r x_r exp(sign 2 pi i r k / R), multiplies by exp(sign 2 pi i j k / m)
+// and writes it back to a[j + k m/R]: every butterfly reads and writes the same
+// R slots, so one buffer and one barrier per stage suffice.  The result is in
+// digit-reversed order: frequency k is at fft_dif_pos(k).
+template <int R, typename C>
+__device__ __forceinline__ void fft_stage_dif(C *a, int n, int nl, int m, int sign,
+                                              const C *__restrict__ tw, const LineMap &lm) {
+  if ((int)threadIdx.x >= lm.lanes) return;
+  const int mr = m / R;          // butterfly stride within a block
+  const int tws = n / m;         // table step of exp(sign 2 pi i / m)
+  const FastDiv dmr = make_fastdiv((unsigned)mr);
+  const int nbf = n / R;
+  for (int idx = lm.i0; idx < nbf; idx += lm.step) {
+    const int b = (int)fdiv((unsigned)idx, dmr), j = idx - b * mr;
+    C *base = a + (b * m + j) * nl + lm.l;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = base[r * mr * nl];
+    bfly<R>(v, sign);
+    if (j > 0) {
+#pragma unroll
+      for (int k = 1; k < R; ++k) {
+        C t = tw[j * k * tws];
+        if (sign > 0) t.y = -t.y;
+        v[k] = cmul(v[k], t);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < R; ++k) base[k * mr * nl] = v[k];
+  }
+}
+
+// Run all stages of plan `pl` in place on a (nl interleaved lines: element e of
+// line l at a[e nl + l]).  Call after a barrier; ends with a barrier.
+template <typename C>
+__device__ void fft_exec_dif(C *a, int n, int nl, const FftPlanDev &pl, int sign, const C *tw) {
+  const LineMap lm = line_map(nl);
+  int m = n;
+  for (int s = 0; s < pl.nstages; ++s) {
+    const int R = pl.radix[s];
+    switch (R) {
+      case 8: fft_stage_dif<8>(a, n, nl, m, sign, tw, lm); break;
+      case 4: fft_stage_dif<4>(a, n, nl, m, sign, tw, lm); break;
+      case 2: fft_stage_dif<2>(a, n, nl, m, sign, tw, lm); break;
+      case 3: fft_stage_dif<3>(a, n, nl, m, sign, tw, lm); break;
+      case 5: fft_stage_dif<5>(a, n, nl, m, sign, tw, lm); break;
+    }
+    __syncthreads();
+    m /= R;
+  }
+}
+
+// Buffer slot of frequency k after fft_exec_dif: with k = d0 + R0 d1 + R0 R1 d2 + ...,
+// slot = d0 n/R0 + d1 n/(R0 R1) + ...
+__device__ __forceinline__ int fft_dif_pos(int k, const FftPlanDev &pl) {
+  int p = 0, span = pl.n;
+#pragma unroll 1
+  for (int s = 0; s < pl.nstages; ++s) {
+    const int R = pl.radix[s];
+    span = div_radix(span, R);
+    const int q = div_radix(k, R);
+    p += (k - q * R) * span;
+    k = q;
+  }
+  return p;
+}
+
 }  // namespace fio

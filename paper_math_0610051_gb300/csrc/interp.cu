@@ -41,6 +41,8 @@ constexpr unsigned kFull = 0xffffffffu;
 constexpr int kInterpSmemG = 96 * 1024;   // footprint staging buffer of S3
 constexpr int kSpreadSmem = 100 * 1024;   // dynamic shared memory budget of S4a
 constexpr int kCand = 256;                // candidate points per S4a chunk
+constexpr int kStrip = 4;                 // adjacent cells of one row per S4a lane group
+constexpr int kChunk = 192;               // points per S3 chunk (weights and alpha staged)
 constexpr int kMaxRegion = (kBin + kMaxKbWidth - 1) * (kBin + kMaxKbWidth - 1);
 
 int host_mod(int a, int m) {
@@ -99,9 +101,10 @@ __device__ __forceinline__ int2 point_weights(uint2 Y, int m1, int m2, const KbD
   return make_int2(imodp(j01, m1), imodp(j02, m2));
 }
 
-// Copy `nu` units (starting at complex channel cbase) of every footprint cell into
-// sG, cell-major: sG[cell * nu + k].  Warp wid copies rows wid, wid + 8, ...; a
-// row's units are contiguous in global memory when the grid holds one input.
+// Start copying `nu` units (starting at complex channel cbase) of every footprint
+// cell into sG, cell-major: sG[cell * nu + k] (asynchronous: cp_async_wait and a
+// barrier complete it).  Warp wid copies rows wid, wid + 8, ...; a row's units
+// are contiguous in global memory when the grid holds one input.
 template <typename T>
 __device__ __forceinline__ void stage_cells(uint4 *sG, const Cx<T> *gw, int4 tl, int m1, int m2,
                                             long long nch, long long cbase, int nu) {
@@ -116,7 +119,7 @@ __device__ __forceinline__ void stage_cells(uint4 *sG, const Cx<T> *gw, int4 tl,
     for (int e = lane; e < tl.w * nu; e += 32) {
       int g2 = tl.y + f2;
       while (g2 >= m2) g2 -= m2;
-      rowdst[e] = reinterpret_cast<const uint4 *>(rowsrc + (long long)g2 * nch)[k];
+      cp_async<16>(&rowdst[e], reinterpret_cast<const uint4 *>(rowsrc + (long long)g2 * nch) + k);
       f2 += sf2;
       k += sk;
       if (k >= nu) {
@@ -145,7 +148,33 @@ __device__ __forceinline__ void add_out(double2 *o, double re, double im) {
   atomicAdd(&o->y, im);
 }
 
+// A 16-byte unit of rank terms: two complex64 terms or one complex128 term.
+template <typename T> struct UnitT;
+template <> struct UnitT<float> { using type = float4; };
+template <> struct UnitT<double> { using type = double2; };
+__device__ __forceinline__ void ufma(float4 &a, float w, const float4 &v) {
+  a.x = fmaf(w, v.x, a.x);
+  a.y = fmaf(w, v.y, a.y);
+  a.z = fmaf(w, v.z, a.z);
+  a.w = fmaf(w, v.w, a.w);
+}
+__device__ __forceinline__ void ufma(double2 &a, double w, const double2 &v) {
+  a.x = fma(w, v.x, a.x);
+  a.y = fma(w, v.y, a.y);
+}
+template <typename U, typename T> __device__ __forceinline__ void ufma4(U &a, T w, const U &v) {
+  ufma(a, w, v);
+}
+template <typename U> __device__ __forceinline__ U uzero();
+template <> __device__ __forceinline__ float4 uzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
+template <> __device__ __forceinline__ double2 uzero<double2>() { return make_double2(0.0, 0.0); }
+
 // -------------------------------------------------------------------- S3 ---
+
+// Points that share a window start are interpolated together: a lane group
+// takes a task of up to kRun such points, loads every footprint unit of their
+// common window once and applies it to each of them.
+template <typename T> struct RunLen { static constexpr int value = sizeof(T) == 4 ? 4 : 2; };
 
 template <typename T, int W>
 __global__ void __launch_bounds__(256, 2)
@@ -155,10 +184,16 @@ k_interp_bin(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
              Cx<T> *__restrict__ out, long long NN, int B, KbDev kb, HornerDev hz, int smem_g,
              int *errw) {
   using C = Cx<T>;
+  using U = typename UnitT<T>::type;
+  constexpr int kRun = RunLen<T>::value;
+  __shared__ int sKey[kChunk];   // window start (dr kBin + dc) of each point, -1: skip
+  __shared__ int sTask[kChunk];  // tasks: first point | count << 16
+  __shared__ uint32_t sPm[kChunk];  // output index x of each point
+  __shared__ int sNT;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  uint4 *sG = reinterpret_cast<uint4 *>(smem_raw);
+  U *sG = reinterpret_cast<U *>(smem_raw);
   T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw + smem_g);
-  int2 *sOff = reinterpret_cast<int2 *>(smem_raw + smem_g + 256 * 2 * W * sizeof(T));
+  U *sAl = reinterpret_cast<U *>(smem_raw + smem_g + kChunk * 2 * W * sizeof(T));  // alpha, one pass
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int4 it = items[blockIdx.x];
   const int l = it.x;
@@ -168,7 +203,9 @@ k_interp_bin(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
   const int r0 = (it.y / nb2) * kBin, c0 = (it.y % nb2) * kBin;
   const int H1 = min(kBin, m1 - r0), H2 = min(kBin, m2 - c0);
   const int4 tl = make_int4(r0, c0, H1 + W - 1, H2 + W - 1);
-  const int CHU = min(min(nu, 32), smem_g / 16 / (tl.z * tl.w));
+  // units per pass: the launcher's figure for the largest footprint, so that the
+  // alpha buffer (kChunk x CHU units) is never overrun, even in a smaller edge bin
+  const int CHU = min(min(nu, 32), smem_g / 16 / ((kBin + W - 1) * (kBin + W - 1)));
   const long long nch = (long long)B * qp;
   const C *gw = grid + Wd[l].grid_unit * B;
   const C *al = alpha + Wd[l].alpha_off;
@@ -178,83 +215,96 @@ k_interp_bin(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
     for (int u0 = 0; u0 < nu; u0 += CHU) {
       const int nuc = min(CHU, nu - u0);
       const long long cbase = (long long)b * qp + (long long)u0 * cpu;
-      __syncthreads();  // the previous pass is done with sG
-      stage_cells<T>(sG, gw, tl, m1, m2, nch, cbase, nuc);
-      const int gpw = 32 / nuc;  // point groups per warp
+      __syncthreads();  // the previous pass is done with sG, sWt, sKey, sTask
+      stage_cells<T>(reinterpret_cast<uint4 *>(sG), gw, tl, m1, m2, nch, cbase, nuc);
+      const int gpw = 32 / nuc;  // lane groups per warp
       const int g = lane / nuc, k = lane - g * nuc;
-      const int stride = 8 * gpw;
-      for (int c = it.z; c < it.w; c += 256) {
-        const int np = min(256, it.w - c);
-        __syncthreads();  // footprint staged; the previous chunk is done with sWt, sOff
-        if (tid < np) {
-          int2 off = make_int2(-1, -1);
+      const int ngr = 8 * gpw;
+      for (int c = it.z; c < it.w; c += kChunk) {
+        const int np = min(kChunk, it.w - c);
+        if (c != it.z) __syncthreads();  // the previous chunk is done with sWt, sAl, sKey, sTask
+        if (tid == 0) sNT = 0;
+        // units u0 .. u0 + nuc of the chunk's alpha rows (one contiguous run when
+        // nuc = nu): sAl[p * nuc + kk]
+        {
+          const U *src = reinterpret_cast<const U *>(al + (long long)c * qp) + u0;
+          const FastDiv dnu = make_fastdiv((unsigned)nuc);
+          for (int e = tid; e < np * nuc; e += 256) {
+            const int pt = (int)fdiv((unsigned)e, dnu), kk = e - pt * nuc;
+            cp_async<16>(sAl + e, src + pt * nu + kk);
+          }
+        }
+        if (tid < np) {  // overlaps the copies in flight
+          int key = -1;
+          sPm[tid] = pm[c + tid];
           const int2 sc = point_weights<T, W>(ws[c + tid], m1, m2, kb, hz, sWt[tid]);
           const int dr = sc.x - r0, dc = sc.y - c0;
-          if (dr >= 0 && dr < H1 && dc >= 0 && dc < H2) off = make_int2(dr, dc);
+          if (dr >= 0 && dr < H1 && dc >= 0 && dc < H2) key = dr * kBin + dc;
           else atomicOr(errw, 1);
-          sOff[tid] = off;
+          sKey[tid] = key;
+        }
+        cp_async_wait();
+        __syncthreads();  // footprint and alpha staged, windows ready
+        if (tid < np) {   // runs of equal window start, cut into tasks of <= kRun points
+          const int key = sKey[tid];
+          if (key >= 0 && (tid == 0 || sKey[tid - 1] != key)) {
+            int len = 1;
+            while (tid + len < np && sKey[tid + len] == key) ++len;
+            for (int s0 = 0; s0 < len; s0 += kRun)
+              sTask[atomicAdd(&sNT, 1)] = (tid + s0) | (min(kRun, len - s0) << 16);
+          }
         }
         __syncthreads();
-        for (int q0 = 0; q0 < np; q0 += stride) {
-          const int pi = q0 + wid * gpw + g;
-          const bool act = g < gpw && pi < np;
-          const int2 off = act ? sOff[pi] : make_int2(-1, -1);
-          T re = 0, im = 0;
-          if (off.x >= 0) {
-            const T *wp = sWt[pi];
-            const int t = (u0 + k) * cpu;
-            const C *al_pt = al + (long long)(c + pi) * qp + t;
-            if constexpr (sizeof(T) == 4) {
-              float ax = 0.f, ay = 0.f, bx = 0.f, by = 0.f;
+        const int ntask = sNT;
+        for (int q0 = 0; q0 < ntask; q0 += ngr) {  // uniform per warp: shuffles below
+          const int task = q0 + wid * gpw + g;
+          const bool act = g < gpw && task < ntask;
+          const int tk = act ? sTask[task] : 0;
+          const int p0 = tk & 0xffff, cnt = act ? tk >> 16 : 0;
+          const int key = act ? sKey[p0] : 0;
+          const int dr = key / kBin, dc = key - dr * kBin;
+          T w2[kRun][W];
 #pragma unroll
-              for (int a1 = 0; a1 < W; ++a1) {
-                float rax = 0.f, ray = 0.f, rbx = 0.f, rby = 0.f;
-                const float4 *pr =
-                    reinterpret_cast<const float4 *>(sG) + ((off.x + a1) * tl.w + off.y) * nuc + k;
+          for (int r = 0; r < kRun; ++r)
 #pragma unroll
-                for (int a2 = 0; a2 < W; ++a2) {
-                  const float4 gv = pr[a2 * nuc];
-                  const float w2 = wp[W + a2];
-                  rax = fmaf(w2, gv.x, rax);
-                  ray = fmaf(w2, gv.y, ray);
-                  rbx = fmaf(w2, gv.z, rbx);
-                  rby = fmaf(w2, gv.w, rby);
-                }
-                const float w1 = wp[a1];
-                ax = fmaf(w1, rax, ax);
-                ay = fmaf(w1, ray, ay);
-                bx = fmaf(w1, rbx, bx);
-                by = fmaf(w1, rby, by);
+            for (int a = 0; a < W; ++a) w2[r][a] = r < cnt ? sWt[p0 + r][W + a] : T(0);
+          U acc[kRun];
+#pragma unroll
+          for (int r = 0; r < kRun; ++r) acc[r] = uzero<U>();
+          if (act) {
+#pragma unroll
+            for (int a1 = 0; a1 < W; ++a1) {
+              const U *pr = sG + ((dr + a1) * tl.w + dc) * nuc + k;
+              U rp[kRun];
+#pragma unroll
+              for (int r = 0; r < kRun; ++r) rp[r] = uzero<U>();
+#pragma unroll
+              for (int a2 = 0; a2 < W; ++a2) {
+                const U gv = pr[a2 * nuc];
+#pragma unroll
+                for (int r = 0; r < kRun; ++r) ufma(rp[r], w2[r][a2], gv);
               }
-              const float4 a = *reinterpret_cast<const float4 *>(al_pt);
-              re = a.x * ax - a.y * ay + a.z * bx - a.w * by;
-              im = a.x * ay + a.y * ax + a.z * by + a.w * bx;
-            } else {
-              double ax = 0.0, ay = 0.0;
 #pragma unroll
-              for (int a1 = 0; a1 < W; ++a1) {
-                double rax = 0.0, ray = 0.0;
-                const double2 *pr =
-                    reinterpret_cast<const double2 *>(sG) + ((off.x + a1) * tl.w + off.y) * nuc + k;
-#pragma unroll
-                for (int a2 = 0; a2 < W; ++a2) {
-                  const double2 gv = pr[a2 * nuc];
-                  const double w2 = wp[W + a2];
-                  rax = fma(w2, gv.x, rax);
-                  ray = fma(w2, gv.y, ray);
-                }
-                const double w1 = wp[a1];
-                ax = fma(w1, rax, ax);
-                ay = fma(w1, ray, ay);
-              }
-              const C a = *al_pt;
-              re = a.x * ax - a.y * ay;
-              im = a.x * ay + a.y * ax;
+              for (int r = 0; r < kRun; ++r) ufma4(acc[r], r < cnt ? sWt[p0 + r][a1] : T(0), rp[r]);
             }
           }
-          re = group_sum(re, k, nuc);
-          im = group_sum(im, k, nuc);
-          if (act && k == 0 && off.x >= 0) add_out(out + (long long)b * NN + pm[c + pi], re, im);
+#pragma unroll
+          for (int r = 0; r < kRun; ++r) {
+            T re = 0, im = 0;
+            if (r < cnt) {
+              const U a = sAl[(p0 + r) * nuc + k];
+              if constexpr (sizeof(T) == 4) {
+                re = a.x * acc[r].x - a.y * acc[r].y + a.z * acc[r].z - a.w * acc[r].w;
+                im = a.x * acc[r].y + a.y * acc[r].x + a.z * acc[r].w + a.w * acc[r].z;
+              } else {
+                re = a.x * acc[r].x - a.y * acc[r].y;
+                im = a.x * acc[r].y + a.y * acc[r].x;
+              }
+            }
+            re = group_sum(re, k, nuc);
+            im = group_sum(im, k, nuc);
+            if (k == 0 && r < cnt) add_out(out + (long long)b * NN + sPm[p0 + r], re, im);
+          }
         }
       }
     }
@@ -273,14 +323,18 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
   using C = Cx<T>;
   __shared__ int sRS[kMaxRegion + 1];  // region-ordered first candidate of every start cell
   __shared__ int sGB[kMaxRegion];      // sorted position of every start cell's first point
+  using U = typename UnitT<T>::type;
+  // candidate weights: w1[a] at [a], then w2 zero-padded by kStrip - 1 on both
+  // sides, so that the kStrip cells of a strip read kStrip consecutive entries
+  constexpr int WS = 2 * W + 2 * kStrip - 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw);
-  C *sIn = reinterpret_cast<C *>(smem_raw + kCand * 2 * W * sizeof(T));
+  T(*sWt)[WS] = reinterpret_cast<T(*)[WS]>(smem_raw);
+  C *sIn = reinterpret_cast<C *>(smem_raw + kCand * WS * sizeof(T));
   int *sPos = reinterpret_cast<int *>(sIn + kCand);
   unsigned char *sCol = reinterpret_cast<unsigned char *>(sPos + kCand);
-  uint4 *sV = reinterpret_cast<uint4 *>(
-      smem_raw + ((kCand * (2 * W * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16));
-  uint4 *sAcc = sV + kCand * chu;
+  U *sV = reinterpret_cast<U *>(
+      smem_raw + ((kCand * (WS * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16));
+  U *sAcc = sV + kCand * chu;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   const int2 it = bins[blockIdx.x];
   const int l = it.x;
@@ -349,71 +403,78 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
           }
           const int pos = sGB[lo] + (idx - sRS[lo]);
           const int ri = lo / RW, rj = lo - ri * RW;
-          const int2 sc = point_weights<T, W>(ws[pos], m1, m2, kb, hz, sWt[tid]);
-          if (sc.x != imodp(r0 - (W - 1) + ri, m1) || sc.y != imodp(c0 - (W - 1) + rj, m2)) {
-            atomicOr(errw, 1);
+          T wt[2 * W];
+          const int2 sc = point_weights<T, W>(ws[pos], m1, m2, kb, hz, wt);
+          const bool ok = sc.x == imodp(r0 - (W - 1) + ri, m1) && sc.y == imodp(c0 - (W - 1) + rj, m2);
+          if (!ok) atomicOr(errw, 1);
 #pragma unroll
-            for (int a = 0; a < 2 * W; ++a) sWt[tid][a] = T(0);
+          for (int a = 0; a < W; ++a) {
+            sWt[tid][a] = ok ? wt[a] : T(0);
+            sWt[tid][W + kStrip - 1 + a] = ok ? wt[W + a] : T(0);
+          }
+#pragma unroll
+          for (int j = 0; j < kStrip - 1; ++j) {
+            sWt[tid][W + j] = T(0);
+            sWt[tid][2 * W + kStrip - 1 + j] = T(0);
           }
           sPos[tid] = pos;
           sCol[tid] = (unsigned char)rj;
           sIn[tid] = gin[(long long)b * NN + pm[pos]];
         }
         __syncthreads();
-        // conj(alpha_t) g for units u0 .. u0 + nuc of every candidate
+        // conj(alpha_t) g for units u0 .. u0 + nuc of every candidate: alpha is
+        // copied asynchronously into sV, then multiplied in place by the thread
+        // that copied it
         for (int e = tid; e < np * nuc; e += 256) {
           const int t = e / nuc, kk = e - t * nuc;
-          const C gv = sIn[t];
-          const C *ap = al + (long long)sPos[t] * qp + (u0 + kk) * cpu;
+          cp_async<16>(sV + e, al + (long long)sPos[t] * qp + (u0 + kk) * cpu);
+        }
+        cp_async_wait();
+        for (int e = tid; e < np * nuc; e += 256) {
+          const C gv = sIn[e / nuc];
           if constexpr (sizeof(T) == 4) {
-            const float4 a = *reinterpret_cast<const float4 *>(ap);
+            const float4 a = reinterpret_cast<const float4 *>(sV)[e];
             const C v0 = cmulc(gv, C{a.x, a.y}), v1 = cmulc(gv, C{a.z, a.w});
-            reinterpret_cast<float4 *>(sV)[t * nuc + kk] = make_float4(v0.x, v0.y, v1.x, v1.y);
+            reinterpret_cast<float4 *>(sV)[e] = make_float4(v0.x, v0.y, v1.x, v1.y);
           } else {
-            reinterpret_cast<double2 *>(sV)[t * nuc + kk] = cmulc(gv, *ap);
+            double2 *v = reinterpret_cast<double2 *>(sV) + e;
+            *v = cmulc(gv, *v);
           }
         }
         __syncthreads();
         if (g < gpw) {
-          for (int cell = wid * gpw + g; cell < H1 * H2; cell += ngr) {
-            const int rl = cell / H2, cl = cell - rl * H2;
-            if constexpr (sizeof(T) == 4) {
-              float4 acc = ch == 0 ? make_float4(0.f, 0.f, 0.f, 0.f)
-                                   : reinterpret_cast<const float4 *>(sAcc)[cell * nuc + k];
-              for (int a1 = 0; a1 < W; ++a1) {
-                const int rb = (rl + W - 1 - a1) * RW + cl;
-                const int lo = max(sRS[rb] - c, 0), hi = min(sRS[rb + W] - c, np);
-                for (int t = lo; t < hi; ++t) {
-                  const float wt = sWt[t][a1] * sWt[t][W + cl + W - 1 - sCol[t]];
-                  const float4 v = reinterpret_cast<const float4 *>(sV)[t * nuc + k];
-                  acc.x = fmaf(wt, v.x, acc.x);
-                  acc.y = fmaf(wt, v.y, acc.y);
-                  acc.z = fmaf(wt, v.z, acc.z);
-                  acc.w = fmaf(wt, v.w, acc.w);
-                }
+          // a group owns kStrip adjacent cells (rl, cl0 + j) of one row; for window
+          // row a1 the points that reach them have start cells in region row
+          // rl + W - 1 - a1, columns cl0 .. cl0 + kStrip + W - 2: one contiguous run
+          const int nsc = (H2 + kStrip - 1) / kStrip;
+          for (int st = wid * gpw + g; st < H1 * nsc; st += ngr) {
+            const int rl = st / nsc, cl0 = (st - rl * nsc) * kStrip;
+            const int kc = min(kStrip, H2 - cl0);
+            const int cend = min(cl0 + kStrip + W - 1, RW);
+            U acc[kStrip];
+#pragma unroll
+            for (int j = 0; j < kStrip; ++j)
+              acc[j] = (ch == 0 || j >= kc) ? uzero<U>() : sAcc[(rl * H2 + cl0 + j) * nuc + k];
+            for (int a1 = 0; a1 < W; ++a1) {
+              const int rb = (rl + W - 1 - a1) * RW;
+              const int lo = max(sRS[rb + cl0] - c, 0), hi = min(sRS[rb + cend] - c, np);
+              for (int t = lo; t < hi; ++t) {
+                const T *wr = sWt[t];
+                const T w1 = wr[a1];
+                const T *w2 = wr + (W + cl0 + W + kStrip - 2 - sCol[t]);
+                const U v = sV[t * nuc + k];
+#pragma unroll
+                for (int j = 0; j < kStrip; ++j) ufma(acc[j], w1 * w2[j], v);
               }
+            }
+#pragma unroll
+            for (int j = 0; j < kStrip; ++j) {
+              if (j >= kc) break;
               if (ch == nchunks - 1)
-                *reinterpret_cast<float4 *>(gw + ((long long)(r0 + rl) * m2 + c0 + cl) * nch +
-                                            (long long)b * qp + (u0 + k) * cpu) = acc;
+                *reinterpret_cast<U *>(gw + ((long long)(r0 + rl) * m2 + c0 + cl0 + j) * nch +
+                                       (long long)b * qp + (u0 + k) * cpu) = acc[j];
               else
-                reinterpret_cast<float4 *>(sAcc)[cell * nuc + k] = acc;
-            } else {
-              double2 acc = ch == 0 ? make_double2(0.0, 0.0)
-                                    : reinterpret_cast<const double2 *>(sAcc)[cell * nuc + k];
-              for (int a1 = 0; a1 < W; ++a1) {
-                const int rb = (rl + W - 1 - a1) * RW + cl;
-                const int lo = max(sRS[rb] - c, 0), hi = min(sRS[rb + W] - c, np);
-                for (int t = lo; t < hi; ++t) {
-                  const double wt = sWt[t][a1] * sWt[t][W + cl + W - 1 - sCol[t]];
-                  const double2 v = reinterpret_cast<const double2 *>(sV)[t * nuc + k];
-                  acc.x = fma(wt, v.x, acc.x);
-                  acc.y = fma(wt, v.y, acc.y);
-                }
-              }
-              if (ch == nchunks - 1)
-                gw[((long long)(r0 + rl) * m2 + c0 + cl) * nch + (long long)b * qp + (u0 + k)] = acc;
-              else
-                reinterpret_cast<double2 *>(sAcc)[cell * nuc + k] = acc;
+                sAcc[(rl * H2 + cl0 + j) * nuc + k] = acc[j];
             }
           }
         }
@@ -439,7 +500,8 @@ cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, voi
   const int numax = std::min(32, max_units<T>(p));
   cudaError_t e;
   if (spread) {
-    const size_t fixed = (kCand * (2 * W * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16;
+    const size_t fixed =
+        (kCand * ((2 * W + 2 * kStrip - 2) * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16;
     const size_t per_unit = (size_t)(kCand + kBin * kBin) * 16;
     const int chu = (int)std::max<long long>(
         1, std::min<long long>(numax, ((long long)kSpreadSmem - (long long)fixed) / (long long)per_unit));
@@ -456,7 +518,7 @@ cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, voi
     const int cells = (kBin + W - 1) * (kBin + W - 1);
     const int chu = std::max(1, std::min(numax, kInterpSmemG / (16 * cells)));
     const int smem_g = chu * 16 * cells;
-    const size_t smem = (size_t)smem_g + 256 * 2 * W * sizeof(T) + 256 * sizeof(int2);
+    const size_t smem = (size_t)smem_g + kChunk * 2 * W * sizeof(T) + (size_t)kChunk * chu * 16;
     e = cudaFuncSetAttribute(k_interp_bin<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
