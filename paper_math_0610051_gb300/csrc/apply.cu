@@ -137,8 +137,11 @@ k_scatter_rowfft(const Cx<T> *__restrict__ fhat, const WedgeDev *__restrict__ W,
   const int nlc = min(nl, nch - c0);
   C *a = reinterpret_cast<C *>(smem_raw);
   C *tw = a + n * nl;
+  short *pos = reinterpret_cast<short *>(tw + n);
+  const FftPlanDev pl = ffts[w.fft2];
   for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw2_off + k];
   for (int k = threadIdx.x; k < n * nlc; k += blockDim.x) a[k] = C{0, 0};
+  fft_dif_table(pos, pl);
   __syncthreads();
   const int k1pp = rw.xi1 + w.xc1;
   const LineMap lm = line_map(nlc);
@@ -156,12 +159,10 @@ k_scatter_rowfft(const Cx<T> *__restrict__ fhat, const WedgeDev *__restrict__ W,
     }
   }
   __syncthreads();
-  const FftPlanDev pl = ffts[w.fft2];
   fft_exec_dif(a, n, nlc, pl, +1, tw);
   C *out = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * n * nch + c0;
   if ((int)threadIdx.x < lm.lanes)
-    for (int e = lm.i0; e < n; e += lm.step)
-      out[(long long)e * nch + lm.l] = a[fft_dif_pos(e, pl) * nlc + lm.l];
+    for (int e = lm.i0; e < n; e += lm.step) out[(long long)e * nch + lm.l] = a[pos[e] * nlc + lm.l];
 }
 
 // ------------------------------------------------------------ S2 / S4b -----
@@ -193,8 +194,11 @@ k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   const int n = w.m1;
   C *a = reinterpret_cast<C *>(smem_raw);
   C *tw = a + n * nl;
+  short *pos = reinterpret_cast<short *>(tw + n);
+  const FftPlanDev pl = ffts[w.fft1];
   C *g = grid + w.grid_unit * B + cc0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw1_off + k];
+  fft_dif_table(pos, pl);
   const LineMap lm = line_map(nlc);
   const bool on = (int)threadIdx.x < lm.lanes;
   const int c = lm.l;
@@ -211,15 +215,14 @@ k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   }
   cp_async_wait();
   __syncthreads();
-  const FftPlanDev pl = ffts[w.fft1];
   fft_exec_dif(a, n, nlc, pl, adjoint ? -1 : +1, tw);
   if (!on) return;
   if (!adjoint) {
-    for (int e = lm.i0; e < n; e += lm.step) g[e * rs + c] = a[fft_dif_pos(e, pl) * nlc + c];
+    for (int e = lm.i0; e < n; e += lm.step) g[e * rs + c] = a[pos[e] * nlc + c];
   } else {
     for (int e = lm.i0; e < w.n1; e += lm.step) {
       const int g1 = imodp(w.b1 + e, n);
-      g[g1 * rs + c] = a[fft_dif_pos(g1, pl) * nlc + c];
+      g[g1 * rs + c] = a[pos[g1] * nlc + c];
     }
   }
 }
@@ -244,8 +247,11 @@ k_rowfft_adj(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   const int nlc = min(nl, nch - c0);
   C *a = reinterpret_cast<C *>(smem_raw);
   C *tw = a + n * nl;
+  short *pos = reinterpret_cast<short *>(tw + n);
+  const FftPlanDev pl = ffts[w.fft2];
   C *row = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * n * nch + c0;
   for (int k = threadIdx.x; k < n; k += blockDim.x) tw[k] = tw_all[w.tw2_off + k];
+  fft_dif_table(pos, pl);
   const LineMap lm = line_map(nlc);
   const bool on = (int)threadIdx.x < lm.lanes;
   if (on)
@@ -253,12 +259,11 @@ k_rowfft_adj(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
       cp_async_elem(&a[e * nlc + lm.l], &row[(long long)e * nch + lm.l]);
   cp_async_wait();
   __syncthreads();
-  const FftPlanDev pl = ffts[w.fft2];
   fft_exec_dif(a, n, nlc, pl, -1, tw);
   if (on)
     for (int j = lm.i0; j < rw.len; j += lm.step) {
       const int g2 = imodp(rw.a + j, n);
-      row[(long long)g2 * nch + lm.l] = a[fft_dif_pos(g2, pl) * nlc + lm.l];
+      row[(long long)g2 * nch + lm.l] = a[pos[g2] * nlc + lm.l];
     }
 }
 
@@ -346,7 +351,7 @@ struct LaunchGeom {
 };
 
 // Launch shapes of the in-place line FFTs: column blocks, row-chunk count and
-// the largest shared buffers (n * fft_lines(n) + n twiddles).
+// the largest shared buffers (n * fft_lines(n) values, n twiddles, n slots).
 static LaunchGeom geom(const fio_plan_s *p, int B) {
   LaunchGeom g;
   const int prec = p->precision;
@@ -358,8 +363,8 @@ static LaunchGeom geom(const fio_plan_s *p, int B) {
     const int nl1 = fft_lines(w.m1, prec), nl2 = fft_lines(w.m2, prec);
     g.col_blocks += (w.m2 * B * w.qp + nl1 - 1) / nl1;
     g.row_chunks = std::max(g.row_chunks, (B * w.qp + nl2 - 1) / nl2);
-    g.smem_col = std::max(g.smem_col, ((size_t)w.m1 * nl1 + w.m1) * cs);
-    g.smem_row = std::max(g.smem_row, ((size_t)w.m2 * nl2 + w.m2) * cs);
+    g.smem_col = std::max(g.smem_col, ((size_t)w.m1 * nl1 + w.m1) * cs + ((size_t)w.m1 * 2 + 15) / 16 * 16);
+    g.smem_row = std::max(g.smem_row, ((size_t)w.m2 * nl2 + w.m2) * cs + ((size_t)w.m2 * 2 + 15) / 16 * 16);
   }
   return g;
 }

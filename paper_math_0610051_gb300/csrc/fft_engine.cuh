@@ -260,6 +260,13 @@ __device__ void fft_exec_dif(C *a, int n, int nl, const FftPlanDev &pl, int sign
   }
 }
 
+// fft_dif_pos for every k < n into tab (one entry per frequency, shared by all
+// lines of the CTA).  Visible to the block after its next barrier.
+__device__ __forceinline__ int fft_dif_pos(int k, const FftPlanDev &pl);
+__device__ __forceinline__ void fft_dif_table(short *tab, const FftPlanDev &pl) {
+  for (int k = threadIdx.x; k < pl.n; k += blockDim.x) tab[k] = (short)fft_dif_pos(k, pl);
+}
+
 // Buffer slot of frequency k after fft_exec_dif: with k = d0 + R0 d1 + R0 R1 d2 + ...,
 // slot = d0 n/R0 + d1 n/(R0 R1) + ...
 __device__ __forceinline__ int fft_dif_pos(int k, const FftPlanDev &pl) {
