@@ -82,6 +82,12 @@ def allreduce(x, op="max"):
     return float(t.item())
 
 
+def replica_rate(outputs_per_rank, world, ms_max):
+    """Whole-job throughput of `world` independent replicas: every rank's outputs
+    over the slowest rank's time (weak scaling)."""
+    return outputs_per_rank * world / (ms_max / 1e3)
+
+
 def barrier():
     import torch.distributed as dist
     if dist.is_available() and dist.is_initialized():
@@ -324,8 +330,7 @@ def run_ours(a, world, rank, local):
     clocks = sampler.stop()
     ms_max = allreduce(ms, "max")
     launches_all = int(allreduce(launches, "sum"))
-    outputs = 2 * B * N * N * a.steps * world
-    value = outputs / (ms_max / 1e3)
+    value = replica_rate(2 * B * N * N * a.steps, world, ms_max)
 
     # roofline of the dominant stage (largest share of event time)
     sb = stage_bytes(plan, B)

@@ -39,9 +39,8 @@ namespace {
 
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kInterpSmemG = 96 * 1024;   // footprint staging buffer of S3
-constexpr int kSpreadSmem = 100 * 1024;   // dynamic shared memory budget of S4a
+constexpr int kSpreadSmem = 72 * 1024;    // dynamic shared memory budget of S4a
 constexpr int kCand = 256;                // candidate points per S4a chunk
-constexpr int kStrip = 4;                 // adjacent cells of one row per S4a lane group
 constexpr int kChunk = 192;               // points per S3 chunk (weights and alpha staged)
 constexpr int kMaxRegion = (kBin + kMaxKbWidth - 1) * (kBin + kMaxKbWidth - 1);
 
@@ -313,29 +312,35 @@ k_interp_bin(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
 
 // ------------------------------------------------------------------- S4a ---
 
+// The spread sweeps down the columns of a bin.  A lane group (one lane per
+// 16-byte unit) owns cell column cl and walks the region's start rows in order,
+// keeping the w cell rows that a start row can still reach in registers:
+// acc[a1] is cell row i - (w - 1) + a1 while start row i is processed.  A point
+// of start row i and start column rj within w - 1 of the column adds
+// w1[a1] (w2[a2] conj(alpha) g) to acc[a1] for every a1.  After the row, acc[0]
+// is complete (no later start row reaches it): it is written out, and the
+// window slides down.  Candidates come in chunks of kCand in region order; a
+// start row may continue in the next chunk, so the sweep state stays in
+// registers across chunks.
 template <typename T, int W>
-__global__ void __launch_bounds__(256, 2)
+__global__ void __launch_bounds__(256, 3)
 k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
              const WedgeDev *__restrict__ Wd, const int2 *__restrict__ bins,
              const int *__restrict__ cstart, const Cx<T> *__restrict__ alpha,
              const uint2 *__restrict__ warps, const uint32_t *__restrict__ perm, long long NN,
              int B, KbDev kb, HornerDev hz, int chu, int *errw) {
   using C = Cx<T>;
+  using U = typename UnitT<T>::type;
   __shared__ int sRS[kMaxRegion + 1];  // region-ordered first candidate of every start cell
   __shared__ int sGB[kMaxRegion];      // sorted position of every start cell's first point
-  using U = typename UnitT<T>::type;
-  // candidate weights: w1[a] at [a], then w2 zero-padded by kStrip - 1 on both
-  // sides, so that the kStrip cells of a strip read kStrip consecutive entries
-  constexpr int WS = 2 * W + 2 * kStrip - 2;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  T(*sWt)[WS] = reinterpret_cast<T(*)[WS]>(smem_raw);
-  C *sIn = reinterpret_cast<C *>(smem_raw + kCand * WS * sizeof(T));
+  T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw);  // w1 then w2 of each candidate
+  C *sIn = reinterpret_cast<C *>(smem_raw + kCand * 2 * W * sizeof(T));
   int *sPos = reinterpret_cast<int *>(sIn + kCand);
   unsigned char *sCol = reinterpret_cast<unsigned char *>(sPos + kCand);
   U *sV = reinterpret_cast<U *>(
-      smem_raw + ((kCand * (WS * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16));
-  U *sAcc = sV + kCand * chu;
-  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+      smem_raw + ((kCand * (2 * W * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16));
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nth = blockDim.x;
   const int2 it = bins[blockIdx.x];
   const int l = it.x;
   const int m1 = Wd[l].m1, m2 = Wd[l].m2, nb2 = Wd[l].nb2, qp = Wd[l].qp;
@@ -343,7 +348,7 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
   const int nu = qp / cpu;
   const int r0 = (it.y / nb2) * kBin, c0 = (it.y % nb2) * kBin;
   const int H1 = min(kBin, m1 - r0), H2 = min(kBin, m2 - c0);
-  const int RW = H2 + W - 1, RC = (H1 + W - 1) * RW;
+  const int RH = H1 + W - 1, RW = H2 + W - 1, RC = RH * RW;
   const int *cs = cstart + Wd[l].key_off;
   const long long nch = (long long)B * qp;
   C *gw = grid + Wd[l].grid_unit * B;
@@ -353,7 +358,7 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
 
   // Start cells (r0 - W + 1 + ri, c0 - W + 1 + rj) of the region, row-major:
   // their buckets, then an exclusive scan of the bucket sizes.
-  for (int i = tid; i < RC; i += 256) {
+  for (int i = tid; i < RC; i += nth) {
     const int ri = i / RW, rj = i - ri * RW;
     const int s1 = imodp(r0 - (W - 1) + ri, m1), s2 = imodp(c0 - (W - 1) + rj, m2);
     const long long key = bin_key(s1, s2, nb2);
@@ -388,13 +393,19 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
   for (int b = 0; b < B; ++b) {
     for (int u0 = 0; u0 < nu; u0 += chu) {
       const int nuc = min(chu, nu - u0);
-      const int gpw = 32 / nuc, g = lane / nuc, k = lane - g * nuc, ngr = 8 * gpw;
+      const int gpw = 32 / nuc, g = lane / nuc, k = lane - g * nuc;
+      const int cl = wid * gpw + g;  // this group's cell column
+      const bool owner = g < gpw && cl < H2;
+      U acc[W];
+#pragma unroll
+      for (int a = 0; a < W; ++a) acc[a] = uzero<U>();
+      int i = 0;  // next start row of the sweep
       for (int ch = 0; ch < nchunks; ++ch) {
         const int c = ch * kCand;
         const int np = max(0, min(kCand, total - c));
         __syncthreads();  // the previous chunk is done with the candidate arrays
-        if (tid < np) {
-          const int idx = c + tid;
+        for (int t = tid; t < np; t += nth) {
+          const int idx = c + t;
           int lo = 0, hi = RC - 1;  // the start cell holding candidate idx
           while (lo < hi) {
             const int mid = (lo + hi + 1) >> 1;
@@ -408,75 +419,65 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
           const bool ok = sc.x == imodp(r0 - (W - 1) + ri, m1) && sc.y == imodp(c0 - (W - 1) + rj, m2);
           if (!ok) atomicOr(errw, 1);
 #pragma unroll
-          for (int a = 0; a < W; ++a) {
-            sWt[tid][a] = ok ? wt[a] : T(0);
-            sWt[tid][W + kStrip - 1 + a] = ok ? wt[W + a] : T(0);
-          }
-#pragma unroll
-          for (int j = 0; j < kStrip - 1; ++j) {
-            sWt[tid][W + j] = T(0);
-            sWt[tid][2 * W + kStrip - 1 + j] = T(0);
-          }
-          sPos[tid] = pos;
-          sCol[tid] = (unsigned char)rj;
-          sIn[tid] = gin[(long long)b * NN + pm[pos]];
+          for (int a = 0; a < 2 * W; ++a) sWt[t][a] = ok ? wt[a] : T(0);
+          sPos[t] = pos;
+          sCol[t] = (unsigned char)rj;
+          sIn[t] = gin[(long long)b * NN + pm[pos]];
         }
         __syncthreads();
         // conj(alpha_t) g for units u0 .. u0 + nuc of every candidate: alpha is
         // copied asynchronously into sV, then multiplied in place by the thread
         // that copied it
-        for (int e = tid; e < np * nuc; e += 256) {
-          const int t = e / nuc, kk = e - t * nuc;
-          cp_async<16>(sV + e, al + (long long)sPos[t] * qp + (u0 + kk) * cpu);
-        }
-        cp_async_wait();
-        for (int e = tid; e < np * nuc; e += 256) {
-          const C gv = sIn[e / nuc];
-          if constexpr (sizeof(T) == 4) {
-            const float4 a = reinterpret_cast<const float4 *>(sV)[e];
-            const C v0 = cmulc(gv, C{a.x, a.y}), v1 = cmulc(gv, C{a.z, a.w});
-            reinterpret_cast<float4 *>(sV)[e] = make_float4(v0.x, v0.y, v1.x, v1.y);
-          } else {
-            double2 *v = reinterpret_cast<double2 *>(sV) + e;
-            *v = cmulc(gv, *v);
+        {
+          const FastDiv dnu = make_fastdiv((unsigned)nuc);
+          for (int e = tid; e < np * nuc; e += nth) {
+            const int t = (int)fdiv((unsigned)e, dnu), kk = e - t * nuc;
+            cp_async<16>(sV + e, al + (long long)sPos[t] * qp + (u0 + kk) * cpu);
+          }
+          cp_async_wait();
+          for (int e = tid; e < np * nuc; e += nth) {
+            const C gv = sIn[(int)fdiv((unsigned)e, dnu)];
+            if constexpr (sizeof(T) == 4) {
+              const float4 a = reinterpret_cast<const float4 *>(sV)[e];
+              const C v0 = cmulc(gv, C{a.x, a.y}), v1 = cmulc(gv, C{a.z, a.w});
+              reinterpret_cast<float4 *>(sV)[e] = make_float4(v0.x, v0.y, v1.x, v1.y);
+            } else {
+              double2 *v = reinterpret_cast<double2 *>(sV) + e;
+              *v = cmulc(gv, *v);
+            }
           }
         }
         __syncthreads();
-        if (g < gpw) {
-          // a group owns kStrip adjacent cells (rl, cl0 + j) of one row; for window
-          // row a1 the points that reach them have start cells in region row
-          // rl + W - 1 - a1, columns cl0 .. cl0 + kStrip + W - 2: one contiguous run
-          const int nsc = (H2 + kStrip - 1) / kStrip;
-          for (int st = wid * gpw + g; st < H1 * nsc; st += ngr) {
-            const int rl = st / nsc, cl0 = (st - rl * nsc) * kStrip;
-            const int kc = min(kStrip, H2 - cl0);
-            const int cend = min(cl0 + kStrip + W - 1, RW);
-            U acc[kStrip];
-#pragma unroll
-            for (int j = 0; j < kStrip; ++j)
-              acc[j] = (ch == 0 || j >= kc) ? uzero<U>() : sAcc[(rl * H2 + cl0 + j) * nuc + k];
-            for (int a1 = 0; a1 < W; ++a1) {
-              const int rb = (rl + W - 1 - a1) * RW;
-              const int lo = max(sRS[rb + cl0] - c, 0), hi = min(sRS[rb + cend] - c, np);
-              for (int t = lo; t < hi; ++t) {
-                const T *wr = sWt[t];
-                const T w1 = wr[a1];
-                const T *w2 = wr + (W + cl0 + W + kStrip - 2 - sCol[t]);
-                const U v = sV[t * nuc + k];
-#pragma unroll
-                for (int j = 0; j < kStrip; ++j) ufma(acc[j], w1 * w2[j], v);
-              }
+        if (!owner) continue;
+        // sweep the start rows this chunk reaches
+        while (i < RH) {
+          const int rb = i * RW + cl;
+          const int end = sRS[rb + W];
+          const int lo = max(sRS[rb] - c, 0), hi = min(end - c, np);
+#pragma unroll 2
+          for (int t = lo; t < hi; ++t) {
+            const T *wr = sWt[t];
+            const T w2 = wr[W + (cl + W - 1 - sCol[t])];
+            U v = sV[t * nuc + k];
+            v.x *= w2;
+            v.y *= w2;
+            if constexpr (sizeof(T) == 4) {
+              v.z *= w2;
+              v.w *= w2;
             }
 #pragma unroll
-            for (int j = 0; j < kStrip; ++j) {
-              if (j >= kc) break;
-              if (ch == nchunks - 1)
-                *reinterpret_cast<U *>(gw + ((long long)(r0 + rl) * m2 + c0 + cl0 + j) * nch +
-                                       (long long)b * qp + (u0 + k) * cpu) = acc[j];
-              else
-                sAcc[(rl * H2 + cl0 + j) * nuc + k] = acc[j];
-            }
+            for (int a = 0; a < W; ++a) ufma(acc[a], wr[a], v);
           }
+          if (end > c + np) break;  // the start row continues in the next chunk
+          // start row i is complete: cell row i - (W - 1) is final
+          const int rl = i - (W - 1);
+          if (rl >= 0)
+            *reinterpret_cast<U *>(gw + ((long long)(r0 + rl) * m2 + c0 + cl) * nch +
+                                   (long long)b * qp + (long long)(u0 + k) * cpu) = acc[0];
+#pragma unroll
+          for (int a = 0; a < W - 1; ++a) acc[a] = acc[a + 1];
+          acc[W - 1] = uzero<U>();
+          ++i;
         }
       }
     }
@@ -501,15 +502,18 @@ cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, voi
   cudaError_t e;
   if (spread) {
     const size_t fixed =
-        (kCand * ((2 * W + 2 * kStrip - 2) * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16;
-    const size_t per_unit = (size_t)(kCand + kBin * kBin) * 16;
-    const int chu = (int)std::max<long long>(
-        1, std::min<long long>(numax, ((long long)kSpreadSmem - (long long)fixed) / (long long)per_unit));
-    const size_t smem = fixed + per_unit * chu;
+        (kCand * (2 * W * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16;
+    // at most 16 units per pass: two lane groups per warp, at most 8 warps
+    const int chu = std::max(1, std::min(std::min(numax, 16),
+                                         (int)((kSpreadSmem - fixed) / ((size_t)kCand * 16))));
+    const size_t smem = fixed + (size_t)kCand * 16 * chu;
+    // enough lane groups of chu lanes for the kBin columns of a bin
+    const int gpw = 32 / chu;
+    const int threads = 32 * ((kBin + gpw - 1) / gpw);
     e = cudaFuncSetAttribute(k_spread_bin<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    k_spread_bin<T, W><<<p->n_bins, 256, smem, s>>>(
+    k_spread_bin<T, W><<<p->n_bins, threads, smem, s>>>(
         (const C *)in, (C *)grid, p->d_wedges, p->d_bins, p->d_cstart, (const C *)p->d_alpha,
         p->d_warps, p->d_perm, NN, B, make_kbdev(p), p->horner, chu, p->d_errword);
   } else {
