@@ -38,6 +38,48 @@ template <typename C> __device__ __forceinline__ C cmul_si(C a, int sign) {
   return sign > 0 ? C{-a.y, a.x} : C{a.y, -a.x};
 }
 
+// Packed two-wide FP32 arithmetic (sm_100 and later): each lane rounds like the
+// scalar instruction (IEEE, round to nearest), in half the instructions.
+union F2U {
+  float2 f;
+  unsigned long long u;
+};
+__device__ __forceinline__ float2 ffma2(float2 a, float2 b, float2 c) {
+  F2U A, Bv, Cv, D;
+  A.f = a;
+  Bv.f = b;
+  Cv.f = c;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(D.u) : "l"(A.u), "l"(Bv.u), "l"(Cv.u));
+  return D.f;
+}
+__device__ __forceinline__ float2 fmul2(float2 a, float2 b) {
+  F2U A, Bv, D;
+  A.f = a;
+  Bv.f = b;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(D.u) : "l"(A.u), "l"(Bv.u));
+  return D.f;
+}
+__device__ __forceinline__ float2 fadd2(float2 a, float2 b) {
+  F2U A, Bv, D;
+  A.f = a;
+  Bv.f = b;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(D.u) : "l"(A.u), "l"(Bv.u));
+  return D.f;
+}
+__device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
+  F2U A, Bv, D;
+  A.f = a;
+  Bv.f = b;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(D.u) : "l"(A.u), "l"(Bv.u));
+  return D.f;
+}
+template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return fadd2(a, b); }
+template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) { return fsub2(a, b); }
+// (a.x b.x - a.y b.y, a.x b.y + a.y b.x) = (a.x, a.x) (b.x, b.y) + (-a.y, a.y) (b.y, b.x)
+template <> __device__ __forceinline__ float2 cmul<float2>(float2 a, float2 b) {
+  return ffma2(make_float2(-a.y, a.y), make_float2(b.y, b.x), fmul2(make_float2(a.x, a.x), b));
+}
+
 // ---------------------------------------------------------------- butterflies
 // V[k] = sum_r v[r] exp(sign 2 pi i r k / R)
 

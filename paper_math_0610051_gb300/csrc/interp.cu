@@ -152,10 +152,20 @@ template <typename T> struct UnitT;
 template <> struct UnitT<float> { using type = float4; };
 template <> struct UnitT<double> { using type = double2; };
 __device__ __forceinline__ void ufma(float4 &a, float w, const float4 &v) {
-  a.x = fmaf(w, v.x, a.x);
-  a.y = fmaf(w, v.y, a.y);
-  a.z = fmaf(w, v.z, a.z);
-  a.w = fmaf(w, v.w, a.w);
+  const float2 ww = make_float2(w, w);
+  const float2 lo = ffma2(ww, make_float2(v.x, v.y), make_float2(a.x, a.y));
+  const float2 hi = ffma2(ww, make_float2(v.z, v.w), make_float2(a.z, a.w));
+  a = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ void uscale(float4 &v, float w) {
+  const float2 ww = make_float2(w, w);
+  const float2 lo = fmul2(ww, make_float2(v.x, v.y));
+  const float2 hi = fmul2(ww, make_float2(v.z, v.w));
+  v = make_float4(lo.x, lo.y, hi.x, hi.y);
+}
+__device__ __forceinline__ void uscale(double2 &v, double w) {
+  v.x *= w;
+  v.y *= w;
 }
 __device__ __forceinline__ void ufma(double2 &a, double w, const double2 &v) {
   a.x = fma(w, v.x, a.x);
@@ -459,12 +469,7 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
             const T *wr = sWt[t];
             const T w2 = wr[W + (cl + W - 1 - sCol[t])];
             U v = sV[t * nuc + k];
-            v.x *= w2;
-            v.y *= w2;
-            if constexpr (sizeof(T) == 4) {
-              v.z *= w2;
-              v.w *= w2;
-            }
+            uscale(v, w2);
 #pragma unroll
             for (int a = 0; a < W; ++a) ufma(acc[a], wr[a], v);
           }
