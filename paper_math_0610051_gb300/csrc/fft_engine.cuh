@@ -262,8 +262,10 @@ __device__ __forceinline__ void fft_stage_dif(C *a, int n, int nl, int m, int si
   const int tws = n / m;         // table step of exp(sign 2 pi i / m)
   const FastDiv dmr = make_fastdiv((unsigned)mr);
   const int nbf = n / R;
+  // butterfly idx = b mr + j, advanced by step = sb mr + sj without dividing
+  const int sb = (int)fdiv((unsigned)lm.step, dmr), sj = lm.step - sb * mr;
+  int b = (int)fdiv((unsigned)lm.i0, dmr), j = lm.i0 - b * mr;
   for (int idx = lm.i0; idx < nbf; idx += lm.step) {
-    const int b = (int)fdiv((unsigned)idx, dmr), j = idx - b * mr;
     C *base = a + (b * m + j) * nl + lm.l;
     C v[R];
 #pragma unroll
@@ -279,6 +281,12 @@ __device__ __forceinline__ void fft_stage_dif(C *a, int n, int nl, int m, int si
     }
 #pragma unroll
     for (int k = 0; k < R; ++k) base[k * mr * nl] = v[k];
+    b += sb;
+    j += sj;
+    if (j >= mr) {
+      j -= mr;
+      ++b;
+    }
   }
 }
 

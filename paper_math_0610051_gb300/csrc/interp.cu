@@ -42,7 +42,10 @@ constexpr int kInterpSmemG = 96 * 1024;   // footprint staging buffer of S3
 constexpr int kSpreadSmem = 72 * 1024;    // dynamic shared memory budget of S4a
 constexpr int kCand = 256;                // candidate points per S4a chunk
 constexpr int kChunk = 192;               // points per S3 chunk (weights and alpha staged)
-constexpr int kMaxRegion = (kBin + kMaxKbWidth - 1) * (kBin + kMaxKbWidth - 1);
+// S4a works on two horizontally adjacent bins at once (32 columns)
+constexpr int kSpreadCols = 2 * kBin;
+constexpr int kMaxRegion2 = (kBin + kMaxKbWidth - 1) * (kSpreadCols + kMaxKbWidth - 1);
+constexpr int kSpreadMaxUnits = 10;  // units per S4a pass: 3 lane groups per warp, <= 11 warps
 
 int host_mod(int a, int m) {
   const int r = a % m;
@@ -322,7 +325,8 @@ k_interp_bin(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
 
 // ------------------------------------------------------------------- S4a ---
 
-// The spread sweeps down the columns of a bin.  A lane group (one lane per
+// The spread sweeps down the columns of a pair of adjacent bins (16 rows, up to
+// 32 columns).  A lane group (one lane per
 // 16-byte unit) owns cell column cl and walks the region's start rows in order,
 // keeping the w cell rows that a start row can still reach in registers:
 // acc[a1] is cell row i - (w - 1) + a1 while start row i is processed.  A point
@@ -333,7 +337,7 @@ k_interp_bin(const Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ Wd,
 // start row may continue in the next chunk, so the sweep state stays in
 // registers across chunks.
 template <typename T, int W>
-__global__ void __launch_bounds__(256, 3)
+__global__ void __launch_bounds__(384, 2)
 k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
              const WedgeDev *__restrict__ Wd, const int2 *__restrict__ bins,
              const int *__restrict__ cstart, const Cx<T> *__restrict__ alpha,
@@ -341,8 +345,8 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
              int B, KbDev kb, HornerDev hz, int chu, int *errw) {
   using C = Cx<T>;
   using U = typename UnitT<T>::type;
-  __shared__ int sRS[kMaxRegion + 1];  // region-ordered first candidate of every start cell
-  __shared__ int sGB[kMaxRegion];      // sorted position of every start cell's first point
+  __shared__ int sRS[kMaxRegion2 + 1];  // region-ordered first candidate of every start cell
+  __shared__ int sGB[kMaxRegion2];      // sorted position of every start cell's first point
   extern __shared__ __align__(16) unsigned char smem_raw[];
   T(*sWt)[2 * W] = reinterpret_cast<T(*)[2 * W]>(smem_raw);  // w1 then w2 of each candidate
   C *sIn = reinterpret_cast<C *>(smem_raw + kCand * 2 * W * sizeof(T));
@@ -351,13 +355,13 @@ k_spread_bin(const Cx<T> *__restrict__ gin, Cx<T> *__restrict__ grid,
   U *sV = reinterpret_cast<U *>(
       smem_raw + ((kCand * (2 * W * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16));
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5, nth = blockDim.x;
-  const int2 it = bins[blockIdx.x];
+  const int2 it = bins[blockIdx.x];  // (wedge, first bin of a pair in one bin row)
   const int l = it.x;
   const int m1 = Wd[l].m1, m2 = Wd[l].m2, nb2 = Wd[l].nb2, qp = Wd[l].qp;
   constexpr int cpu = 16 / (int)sizeof(C);
   const int nu = qp / cpu;
   const int r0 = (it.y / nb2) * kBin, c0 = (it.y % nb2) * kBin;
-  const int H1 = min(kBin, m1 - r0), H2 = min(kBin, m2 - c0);
+  const int H1 = min(kBin, m1 - r0), H2 = min(kSpreadCols, m2 - c0);
   const int RH = H1 + W - 1, RW = H2 + W - 1, RC = RH * RW;
   const int *cs = cstart + Wd[l].key_off;
   const long long nch = (long long)B * qp;
@@ -508,13 +512,12 @@ cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, voi
   if (spread) {
     const size_t fixed =
         (kCand * (2 * W * sizeof(T) + sizeof(C) + sizeof(int) + 1) + 15) / 16 * 16;
-    // at most 16 units per pass: two lane groups per warp, at most 8 warps
-    const int chu = std::max(1, std::min(std::min(numax, 16),
+    const int chu = std::max(1, std::min(std::min(numax, kSpreadMaxUnits),
                                          (int)((kSpreadSmem - fixed) / ((size_t)kCand * 16))));
     const size_t smem = fixed + (size_t)kCand * 16 * chu;
-    // enough lane groups of chu lanes for the kBin columns of a bin
+    // enough lane groups of chu lanes for the columns of a bin pair
     const int gpw = 32 / chu;
-    const int threads = 32 * ((kBin + gpw - 1) / gpw);
+    const int threads = 32 * ((kSpreadCols + gpw - 1) / gpw);
     e = cudaFuncSetAttribute(k_spread_bin<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
@@ -602,14 +605,15 @@ cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> 
     for (int bin = 0; bin < w.nb1 * w.nb2; ++bin) {
       const int beg = cs[(size_t)bin * kBin * kBin], end = cs[(size_t)(bin + 1) * kBin * kBin];
       for (int c = beg; c < end; c += kItemPts) items.push_back(make_int4(l, bin, c, std::min(end, c + kItemPts)));
-      bins.push_back(make_int2(l, bin));
+      if ((bin % w.nb2) % 2 == 0) bins.push_back(make_int2(l, bin));  // first bin of a pair
       if (end > beg) {
         ++nonempty;
         total += end - beg;
       }
       maxb = std::max(maxb, end - beg);
+      if ((bin % w.nb2) % 2 != 0) continue;  // spread candidates: per bin pair
       const int r0 = (bin / w.nb2) * kBin, c0 = (bin % w.nb2) * kBin;
-      const int RH = std::min(kBin, w.m1 - r0) + W - 1, RW = std::min(kBin, w.m2 - c0) + W - 1;
+      const int RH = std::min(kBin, w.m1 - r0) + W - 1, RW = std::min(kSpreadCols, w.m2 - c0) + W - 1;
       long long cand = 0;
       for (int i = 0; i < RH; ++i) {
         const int s1 = host_mod(r0 - (W - 1) + i, w.m1);

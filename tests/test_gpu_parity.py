@@ -212,6 +212,31 @@ def test_adjoint_sampled_spectrum(env, orc):
     assert rel(ref, got) < 1e-4
 
 
+def test_full_size_bench_configuration(env, orc):
+    """N = 1024, the bench's launch configuration (batch of 8 white-noise inputs,
+    eps = 1e-4, mixed): the forward at 256 random x of inputs 0 and 7 and the
+    adjoint spectrum at 128 random xi of input 3, against the oracle's direct sums."""
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    N, B = 1024, 8
+    prm = synth.ellipse_params()
+    ph = orc.Phase(orc.ELLIPSE, prm)
+    f = synth.white_noise(N, B, seed=10)
+    g = synth.white_noise(N, B, seed=5000, real=False)
+    with fio.Plan(N, fio.PHASE_ELLIPSE, prm, 1e-4, max_batch=B) as plan:
+        out = plan.apply(dev(torch, f, "mixed")).cpu().numpy()
+        adj = plan.adjoint(dev(torch, g, "mixed")).cpu().numpy()
+        plan.sync()
+    n1, n2 = synth.sample_points(N, 256, seed=4)
+    for b in (0, 7):
+        ref = orc.apply_points(ph, orc.Amplitude(), orc.dft2(f[b]), n1, n2)
+        assert rel(ref, out[b][n1, n2]) < 1e-4
+    k1, k2 = synth.sample_freqs(N, 128, seed=5)
+    ref = orc.adjoint_hat_points(ph, orc.Amplitude(), g[3], k1, k2)
+    got = orc.dft2(adj[3])[k1 + N // 2, k2 + N // 2]
+    assert rel(ref, got) < 1e-4
+
+
 # ------------------------------------------------ separation (Table 1) -------
 
 @pytest.mark.parametrize("eps", [1e-4, 1e-6])
