@@ -122,7 +122,10 @@ fio_status fio_plan_create(int N, const fio_phase *phase, const fio_amplitude *a
  * gamma^xi, type-2 NUFFT at the warped points, gamma^x multiply and sum).
  * f, out: device arrays of batch*N*N complex (complex64 for FIO_MIXED plans,
  * complex128 for FIO_FP64).  1 <= batch <= max_batch.  out must not alias f.
- * One plan must not be used on two streams at the same time (shared workspace). */
+ * One plan must not be used on two streams at the same time (shared workspace).
+ * The sum over wedges is accumulated with atomic adds into out, so the last bit
+ * of a result may differ between runs (the order of the additions is not
+ * fixed); every other step, and the whole adjoint, is deterministic. */
 fio_status fio_apply(fio_plan plan, const void *f, void *out, int batch, void *stream);
 
 /* out = L* g (Sec. 3.5: gamma^x-conjugate multiply, type-1 NUFFT, conj(gamma^xi)
