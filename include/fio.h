@@ -134,6 +134,16 @@ fio_status fio_apply(fio_plan plan, const void *f, void *out, int batch, void *s
  * <L f, g> = <f, L* g> holds to rounding. */
 fio_status fio_apply_adjoint(fio_plan plan, const void *g, void *out, int batch, void *stream);
 
+/* out = L* L f, the normal operator (imaging's "migration of the modelled data",
+ * the paper's Figure 2 setting), in one call: fio_apply, then fio_apply_adjoint
+ * of its result, queued on `stream` with no host synchronisation in between.
+ * The intermediate L f is held in out itself (the adjoint reads all of its input
+ * before it writes its output), so the call needs no memory beyond the plan's.
+ * Same layout and rules as fio_apply; out must not alias f.  The result equals
+ * fio_apply_adjoint(fio_apply(f)) up to the rounding order of fio_apply's
+ * atomic sum over wedges. */
+fio_status fio_apply_normal(fio_plan plan, const void *f, void *out, int batch, void *stream);
+
 /* ---------------------------------------------------------------------------
  * Forward apply that allocates nothing.
  *

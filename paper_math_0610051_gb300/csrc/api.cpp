@@ -124,6 +124,19 @@ fio_status fio_apply_adjoint(fio_plan p, const void *g, void *out, int batch, vo
   return e == cudaSuccess ? FIO_OK : cuda_fail(e, "fio_apply_adjoint");
 }
 
+fio_status fio_apply_normal(fio_plan p, const void *f, void *out, int batch, void *stream) {
+  if (!plan_ok(p)) return FIO_EINVAL;
+  if (!f || !out || f == out || batch < 1 || batch > p->max_batch) {
+    set_error("fio_apply_normal: null/aliased pointers or batch outside [1, max_batch]");
+    return FIO_EINVAL;
+  }
+  cudaError_t e = launch_apply(p, f, out, batch, (cudaStream_t)stream);
+  // the adjoint's first stage (the spread) consumes its whole input before any
+  // later stage writes the output, so L f may be read from out in place
+  if (e == cudaSuccess) e = launch_adjoint(p, out, out, batch, (cudaStream_t)stream);
+  return e == cudaSuccess ? FIO_OK : cuda_fail(e, "fio_apply_normal");
+}
+
 fio_status fio_plan_sync(fio_plan p, void *stream) {
   if (!plan_ok(p)) return FIO_EINVAL;
   cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);

@@ -77,7 +77,8 @@ class _WedgeInfo(ctypes.Structure):
 
 # Every symbol include/fio.h declares (checked by the tests).
 EXPORTS = [
-    "fio_options_default", "fio_plan_create", "fio_apply", "fio_apply_adjoint", "fio_apply_noalloc",
+    "fio_options_default", "fio_plan_create", "fio_apply", "fio_apply_adjoint", "fio_apply_normal",
+    "fio_apply_noalloc",
     "fio_plan_sync",
     "fio_plan_get_info", "fio_plan_get_wedge", "fio_plan_export_wedge", "fio_plan_export_warp",
     "fio_plan_destroy", "fio_plan_set_timing", "fio_plan_stage_times",
@@ -105,6 +106,7 @@ def lib():
                                           ctypes.POINTER(_Options), ctypes.POINTER(P)]
             L.fio_apply.argtypes = [P, P, P, I, P]
             L.fio_apply_adjoint.argtypes = [P, P, P, I, P]
+            L.fio_apply_normal.argtypes = [P, P, P, I, P]
             L.fio_apply_noalloc.argtypes = [P, P, P, I, P]
             L.fio_plan_sync.argtypes = [P, P]
             L.fio_plan_get_info.argtypes = [P, ctypes.POINTER(_PlanInfo)]
@@ -245,6 +247,10 @@ class Plan:
     def adjoint(self, g, out=None):
         """out = L* g (fio_apply_adjoint)."""
         return self._run(lib().fio_apply_adjoint, g, out, "fio_apply_adjoint")
+
+    def normal(self, f, out=None):
+        """out = L* L f (fio_apply_normal)."""
+        return self._run(lib().fio_apply_normal, f, out, "fio_apply_normal")
 
     def sync(self):
         _check(lib().fio_plan_sync(self._handle, _stream_ptr(self._torch, self.device)),
