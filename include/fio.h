@@ -74,7 +74,13 @@ typedef struct {
 
 typedef enum {
   FIO_AMP_ONE = 0,       /* a = 1 (the Egorov operator of Sec. 3) */
-  FIO_AMP_SEPARABLE = 1  /* a = (1 + a1 sin 2 pi x1)(1 + a2 cos theta), cos theta := 1 at xi = 0 */
+  FIO_AMP_SEPARABLE = 1, /* a = (1 + a1 sin 2 pi x1)(1 + a2 cos theta), cos theta := 1 at xi = 0 */
+  FIO_AMP_HANKEL = 2     /* integration along ellipses (Appendix A, Eq. ellipses_amp): with
+                            s = a1 (+1 or -1) and rho = s (Phi(x, xi) - x.xi) >= 0,
+                            a = (J0(2 pi rho) + i s Y0(2 pi rho)) exp(-2 pi i s rho) / (4 pi);
+                            the Y0 term is dropped where rho <= 0 (xi = 0).  a2 is unused.
+                            L+ (s = +1, Phi = x.xi + rho) plus L- (s = -1, Phi = x.xi - rho)
+                            integrates f along the ellipses of axes r1, r2 */
 } fio_amp_kind;
 
 typedef struct {

@@ -36,8 +36,14 @@
  * theta = arg(xi) = atan2(xi2, xi1); at xi = 0 the phase is 0 (homogeneity).
  *
  * Amplitude kinds: 0  a = 1;   1  a = (1 + a1 sin 2 pi x1)(1 + a2 cos theta),
- * with cos theta := 1 at xi = 0.
+ * with cos theta := 1 at xi = 0;   2  the Hankel amplitude of the integration
+ * along ellipses (Appendix A, Eq. ellipses_amp): with s = a1 = +1 or -1 and
+ * rho = s (Phi(x, xi) - x.xi),
+ *     a = (J0(2 pi rho) + i s Y0(2 pi rho)) exp(-2 pi i s rho) / (4 pi),
+ * and the Y0 term dropped where rho <= 0 (xi = 0, where Y0 is singular: the
+ * regularisation Appendix A calls for).
  */
+#define _DEFAULT_SOURCE 1 /* j0, y0 (POSIX Bessel functions) from math.h */
 #include <complex.h>
 #include <math.h>
 #include <stdint.h>
@@ -205,8 +211,14 @@ static double psi(const or_phase *ph, const xdata *d, double x1, double x2, int 
   return NAN;
 }
 
-static double amp(const or_amp *a, double x1, int k1, int k2) {
+/* a(x, xi); psi = Phi(x, xi) - x.xi is needed by the Hankel kind only. */
+static cplx amp(const or_amp *a, double x1, int k1, int k2, double psi_val) {
   if (a == NULL || a->kind == 0) return 1.0;
+  if (a->kind == 2) {
+    const double s = a->a1, rho = s * psi_val;
+    const double y = rho > 0 ? y0(TWO_PI * rho) : 0.0;
+    return (j0(TWO_PI * rho) + I * s * y) * cexp(-I * TWO_PI * s * rho) / (2.0 * TWO_PI);
+  }
   double r = sqrt((double)k1 * k1 + (double)k2 * k2);
   double cth = (r > 0) ? (double)k1 / r : 1.0;
   return (1.0 + a->a1 * sin(TWO_PI * x1)) * (1.0 + a->a2 * cth);
@@ -224,10 +236,16 @@ void or_phase_eval(int kind, int nmodes, const double *params, int grouped, int 
   }
 }
 
+/* a(x_i, xi_i) as interleaved complex; psi = Phi - x.xi at the same points (read
+ * by the Hankel kind only, may be NULL otherwise). */
 void or_amp_eval(int kind, double a1, double a2, int npts, const double *x1, const int *k1,
-                 const int *k2, double *out) {
+                 const int *k2, const double *psi_vals, double *out_ri) {
   or_amp a = {kind, a1, a2};
-  for (int i = 0; i < npts; ++i) out[i] = amp(&a, x1[i], k1[i], k2[i]);
+  for (int i = 0; i < npts; ++i) {
+    const cplx v = amp(&a, x1[i], k1[i], k2[i], psi_vals ? psi_vals[i] : 0.0);
+    out_ri[2 * i] = creal(v);
+    out_ri[2 * i + 1] = cimag(v);
+  }
 }
 
 /* tau(x, theta) of the tau-mode phase and its derivatives, by the literal sum
@@ -273,9 +291,10 @@ void or_apply_points(int N, int kind, int nmodes, const double *params, int grou
       int k1 = ik1 - N / 2;
       for (int ik2 = 0; ik2 < N; ++ik2) {
         int k2 = ik2 - N / 2;
+        const double ps = psi(&ph, &d, x1, x2, k1, k2);
         cplx e = tw[imod((long long)n1[i] * k1 + (long long)n2[i] * k2, N)] *
-                 cexp(TWO_PI * I * psi(&ph, &d, x1, x2, k1, k2));
-        s += amp(&am, x1, k1, k2) * e * fh[(size_t)ik1 * N + ik2];
+                 cexp(TWO_PI * I * ps);
+        s += amp(&am, x1, k1, k2, ps) * e * fh[(size_t)ik1 * N + ik2];
       }
     }
     out[i] = s / (double)N;
@@ -323,9 +342,9 @@ void or_adjoint_hat_points(int N, int kind, int nmodes, const double *params, in
     for (size_t i = 0; i < n; ++i) {
       int m1 = (int)(i / N), m2 = (int)(i % N);
       double y1 = (double)m1 / N, y2 = (double)m2 / N;
-      cplx e = tw[imod((long long)m1 * k1[j] + (long long)m2 * k2[j], N)] *
-               cexp(-TWO_PI * I * psi(&ph, &xd[i], y1, y2, k1[j], k2[j]));
-      s += amp(&am, y1, k1[j], k2[j]) * e * g[i]; /* the amplitude is real */
+      const double ps = psi(&ph, &xd[i], y1, y2, k1[j], k2[j]);
+      cplx e = tw[imod((long long)m1 * k1[j] + (long long)m2 * k2[j], N)] * cexp(-TWO_PI * I * ps);
+      s += conj(amp(&am, y1, k1[j], k2[j], ps)) * e * g[i];
     }
     out[j] = s / (double)N;
   }

@@ -30,6 +30,7 @@ _lib = None
 
 # phase kinds of fio_oracle.c
 SHIFT_WAVE, ELLIPSE, TAU_MODES = 0, 1, 2
+AMP_ONE, AMP_SEPARABLE, AMP_HANKEL = 0, 1, 2
 
 
 def build(force: bool = False) -> str:
@@ -129,10 +130,13 @@ def phase_eval(phase: Phase, x1, x2, k1, k2) -> np.ndarray:
     return out
 
 
-def amp_eval(amp: Amplitude, x1, k1, k2) -> np.ndarray:
+def amp_eval(amp: Amplitude, x1, k1, k2, psi=None) -> np.ndarray:
+    """a(x, xi) (complex); psi = Phi - x.xi at the same points is read by the
+    Hankel kind only."""
     x1, k1, k2 = _c(x1, np.float64), _c(k1, np.int32), _c(k2, np.int32)
-    out = np.empty(len(x1), np.float64)
-    _load().or_amp_eval(*amp.args(), len(x1), _p(x1), _p(k1), _p(k2), _p(out))
+    ps = _c(np.zeros(len(x1)) if psi is None else psi, np.float64)
+    out = np.empty(len(x1), np.complex128)
+    _load().or_amp_eval(*amp.args(), len(x1), _p(x1), _p(k1), _p(k2), _p(ps), _p(out))
     return out
 
 

@@ -427,7 +427,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     return FIO_EINVAL;
   }
   const fio_amplitude amp1 = amp ? *amp : fio_amplitude{FIO_AMP_ONE, 0, 0};
-  if (amp1.kind < 0 || amp1.kind > 1 || !std::isfinite(amp1.a1) || !std::isfinite(amp1.a2)) {
+  if (amp1.kind < 0 || amp1.kind > 2 || !std::isfinite(amp1.a1) || !std::isfinite(amp1.a2) ||
+      (amp1.kind == FIO_AMP_HANKEL && amp1.a1 != 1.0 && amp1.a1 != -1.0)) {
     set_error("invalid amplitude");
     return FIO_EINVAL;
   }

@@ -113,11 +113,26 @@ __device__ __forceinline__ void grad_psi_unit(const PhaseDev &ph, const XView &x
   g1 = g2 = 0.0;
 }
 
-__device__ __forceinline__ double amp(const PhaseDev &ph, double x1, int k1, int k2) {
-  if (ph.amp_kind != FIO_AMP_SEPARABLE) return 1.0;
-  const double r = sqrt((double)k1 * k1 + (double)k2 * k2);
-  const double cth = r > 0 ? k1 / r : 1.0;
-  return (1.0 + ph.a1 * sinpi(2.0 * x1)) * (1.0 + ph.a2 * cth);
+// a(x, xi) as a complex number; ps = Phi(x, xi) - x.xi (read by the Hankel kind).
+// Hankel (Appendix A, Eq. ellipses_amp): s = a1, rho = s ps,
+// a = (J0(2 pi rho) + i s Y0(2 pi rho)) exp(-2 pi i s rho) / (4 pi), without the
+// Y0 term where rho <= 0 (xi = 0, where Y0 is singular).
+__device__ __forceinline__ double2 amp(const PhaseDev &ph, double x1, int k1, int k2, double ps) {
+  if (ph.amp_kind == FIO_AMP_SEPARABLE) {
+    const double r = sqrt((double)k1 * k1 + (double)k2 * k2);
+    const double cth = r > 0 ? k1 / r : 1.0;
+    return make_double2((1.0 + ph.a1 * sinpi(2.0 * x1)) * (1.0 + ph.a2 * cth), 0.0);
+  }
+  if (ph.amp_kind == FIO_AMP_HANKEL) {
+    const double s = ph.a1, rho = s * ps;
+    const double z = 2.0 * 3.141592653589793238462643383279502884 * rho;
+    const double jr = j0(z), yi = rho > 0 ? s * y0(z) : 0.0;
+    double sn, cn;
+    sincospi(-2.0 * s * rho, &sn, &cn);
+    const double k = 1.0 / (4.0 * 3.141592653589793238462643383279502884);
+    return make_double2(k * (jr * cn - yi * sn), k * (jr * sn + yi * cn));
+  }
+  return make_double2(1.0, 0.0);
 }
 
 // A_{x,xi} = a(x,xi) exp(2 pi i [Phi(x,xi) - y'.(M xi)]) with y' the 32-bit
@@ -131,11 +146,12 @@ __device__ __forceinline__ double2 entry(const PhaseDev &ph, const XView &xv, in
   const int kk1 = w.M[0] * k1 + w.M[1] * k2, kk2 = w.M[2] * k1 + w.M[3] * k2;
   const uint32_t yk = Y.x * (uint32_t)kk1 + Y.y * (uint32_t)kk2;  // mod 2^32
   const double frac = (double)xx / N - (double)yk * 2.3283064365386962890625e-10;
-  const double phase = frac + psi(ph, xv, x, k1, k2);
+  const double ps = psi(ph, xv, x, k1, k2);
+  const double phase = frac + ps;
   double s, c;
   sincospi(2.0 * phase, &s, &c);
-  const double a = amp(ph, (double)n1 / N, k1, k2);
-  return make_double2(a * c, a * s);
+  const double2 a = amp(ph, (double)n1 / N, k1, k2, ps);
+  return make_double2(a.x * c - a.y * s, a.x * s + a.y * c);
 }
 
 // ------------------------------------------------------------------ kernels --

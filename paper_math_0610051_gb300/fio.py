@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libfio.so")
 
 FIO_OK, FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ERANK, FIO_ETIMEOUT, FIO_EUNSUPPORTED = range(7)
 PHASE_SHIFT_WAVE, PHASE_ELLIPSE, PHASE_TAU_MODES = 0, 1, 2
-AMP_ONE, AMP_SEPARABLE = 0, 1
+AMP_ONE, AMP_SEPARABLE, AMP_HANKEL = 0, 1, 2
 MIXED, FP64 = 0, 1
 
 
@@ -164,7 +164,8 @@ class Plan:
 
     phase: one of PHASE_* with ``params`` (shift/wave: [x01, x02, c]; ellipse:
     [A1, B1, A2, B2]; tau modes: [K, 5] rows {a, k1, k2, m, p}).
-    amp: None (a = 1) or (a1, a2) for a = (1 + a1 sin 2 pi x1)(1 + a2 cos theta).
+    amp: None (a = 1), (a1, a2) for a = (1 + a1 sin 2 pi x1)(1 + a2 cos theta), or
+    ("hankel", s) for the Hankel amplitude of integration along ellipses (s = +1 or -1).
     """
 
     def __init__(self, N: int, phase: int, params, eps: float, amp=None, precision: str = "mixed",
@@ -179,8 +180,12 @@ class Plan:
         self._params = prm
         ph = _Phase(int(phase), len(prm) // 5 if phase == PHASE_TAU_MODES else 0,
                     prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
-        am = _Amp(AMP_ONE, 0.0, 0.0) if amp is None else _Amp(AMP_SEPARABLE, float(amp[0]),
-                                                            float(amp[1]))
+        if amp is None:
+            am = _Amp(AMP_ONE, 0.0, 0.0)
+        elif amp[0] == "hankel":
+            am = _Amp(AMP_HANKEL, float(amp[1]), 0.0)
+        else:
+            am = _Amp(AMP_SEPARABLE, float(amp[0]), float(amp[1]))
         opt = _Options()
         lib().fio_options_default(ctypes.byref(opt))
         opt.precision = FP64 if precision in ("fp64", FP64) else MIXED

@@ -99,3 +99,17 @@ def complex_noise_like(a: np.ndarray, rel: float, seed: int = 0) -> np.ndarray:
     g = _rng(seed)
     n = (g.standard_normal(a.shape) + 1j * g.standard_normal(a.shape)) / np.sqrt(2.0)
     return n * rel * np.sqrt(np.mean(np.abs(a) ** 2))
+
+
+def circle_grt_modes(sign: int = 1) -> np.ndarray:
+    """Tau modes of sign * r(x) with r = (3 + sin 4 pi x1)(3 + sin 4 pi x2) / 16, the
+    circle radius of the variable-amplitude experiment (Sec. 4, Eq. circlerad):
+    r = 9/16 + (3/16) sin 4 pi x1 + (3/16) sin 4 pi x2
+        + (1/32) cos 2 pi (2 x1 - 2 x2) - (1/32) cos 2 pi (2 x1 + 2 x2).
+    With these modes the tau-mode phase is Phi = x.xi + sign r(x) |xi|."""
+    h = np.pi / 2
+    rows = [[9 / 16, 0, 0, 0, 0.0], [3 / 16, 2, 0, 0, -h], [3 / 16, 0, 2, 0, -h],
+            [1 / 32, 2, -2, 0, 0.0], [1 / 32, 2, 2, 0, np.pi]]
+    m = np.array(rows, dtype=np.float64)
+    m[:, 0] *= sign
+    return m

@@ -1,0 +1,50 @@
+"""Pins of the oracle's integration-along-ellipses workload (Sec. 4 variable
+amplitude experiment, Appendix A): the circle radius as tau modes, and the
+identity L+ f + L- f = (1/N) sum_xi J0(2 pi r(x)|xi|)/(2 pi) e^{2 pi i x.xi} fhat(xi),
+the kernel of Appendix A, evaluated here directly with scipy's J0."""
+import numpy as np
+import pytest
+
+from paper_math_0610051_gb300 import synth
+
+sp = pytest.importorskip("scipy.special")
+
+
+def _radius(x1, x2):
+    return (3 + np.sin(4 * np.pi * x1)) * (3 + np.sin(4 * np.pi * x2)) / 16
+
+
+def test_circle_modes_are_the_radius(orc):
+    g = np.random.default_rng(1)
+    x1, x2, th = g.uniform(0, 1, 200), g.uniform(0, 1, 200), g.uniform(0, 2 * np.pi, 200)
+    for sign in (1, -1):
+        tau = orc.tau_eval(synth.circle_grt_modes(sign), x1, x2, th)[:, 0]
+        assert np.max(np.abs(tau - sign * _radius(x1, x2))) < 1e-14
+
+
+def test_hankel_pair_sums_to_the_j0_kernel(orc):
+    N = 32
+    f = synth.white_noise(N, 1, seed=3, real=False)[0]
+    fh = orc.dft2(f)
+    n1, n2 = synth.sample_points(N, 48, seed=2)
+    got = sum(orc.apply_points(orc.Phase(orc.TAU_MODES, synth.circle_grt_modes(s)),
+                               orc.Amplitude(orc.AMP_HANKEL, s), fh, n1, n2) for s in (1, -1))
+    k = np.arange(N) - N // 2
+    K1, K2 = np.meshgrid(k, k, indexing="ij")
+    ref = np.empty(len(n1), complex)
+    for i, (a, b) in enumerate(zip(n1, n2)):
+        x1, x2 = a / N, b / N
+        kern = sp.j0(2 * np.pi * _radius(x1, x2) * np.hypot(K1, K2)) / (2 * np.pi)
+        ref[i] = np.sum(kern * np.exp(2j * np.pi * (x1 * K1 + x2 * K2)) * fh) / N
+    assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+def test_hankel_amplitude_envelope(orc):
+    """|a+-| -> sqrt(2 / (pi z)) / (4 pi) with z = 2 pi rho (Hankel asymptotics),
+    the order -1/2 of Appendix A; the two signs are complex conjugates."""
+    rho = np.array([50.0, 200.0, 800.0])
+    ap = orc.amp_eval(orc.Amplitude(orc.AMP_HANKEL, 1), np.zeros(3), [1] * 3, [0] * 3, rho)
+    am = orc.amp_eval(orc.Amplitude(orc.AMP_HANKEL, -1), np.zeros(3), [1] * 3, [0] * 3, -rho)
+    env = np.sqrt(2 / (np.pi * 2 * np.pi * rho)) / (4 * np.pi)
+    assert np.all(np.abs(np.abs(ap) / env - 1) < 2e-3)
+    assert np.allclose(am, np.conj(ap), rtol=0, atol=1e-15)
