@@ -63,7 +63,12 @@ typedef enum {
   FIO_PHASE_ELLIPSE = 1,
   /* Psi = |xi| tau(x, theta), tau = sum_j a_j cos(2 pi (k1_j x1 + k2_j x2) + m_j theta + p_j);
    * params: nmodes rows {a_j, k1_j, k2_j, m_j, p_j}, m_j an integer in [-8, 8]. */
-  FIO_PHASE_TAU_MODES = 2
+  FIO_PHASE_TAU_MODES = 2,
+  /* Psi = sqrt(r1(x)^2 xi1^2 + r2(x)^2 xi2^2) with product-form axes
+   * r1 = s1 (a1 + sin 4 pi x1)(a1 + sin 4 pi x2), r2 = s2 (a2 + cos 4 pi x1)(a2 + cos 4 pi x2);
+   * params {a1, s1, a2, s2}.  The axes of the paper's own experiments (Sec. 4,
+   * Eq. nrphase and the separation tests of Tables 1-3): a1 = a2 = 2, s1 = s2 = 1/9. */
+  FIO_PHASE_ELLIPSE_PRODUCT = 3
 } fio_phase_kind;
 
 typedef struct {

@@ -30,6 +30,10 @@
  *                   c1 = A1 + B1 sin(2 pi x1) sin(2 pi x2),
  *                   c2 = A2 + B2 cos(2 pi x1) cos(2 pi x2)  params {A1,B1,A2,B2}
  *                   (the phase family of Eq. nrphase)
+ *   3  ellipse with product-form axes (the paper's own experiments, Sec. 4):
+ *                   Psi = sqrt(r1^2 xi1^2 + r2^2 xi2^2),
+ *                   r1 = s1 (a1 + sin 4 pi x1)(a1 + sin 4 pi x2),
+ *                   r2 = s2 (a2 + cos 4 pi x1)(a2 + cos 4 pi x2)  params {a1,s1,a2,s2}
  *   2  tau modes    Psi = |xi| tau(x, theta),
  *                   tau = sum_j a_j cos(2 pi (k1_j x1 + k2_j x2) + m_j theta + p_j)
  *                   params: nmodes rows of {a_j, k1_j, k2_j, m_j, p_j}
@@ -159,6 +163,10 @@ static void prepare_x(const or_phase *ph, double x1, double x2, int grouped, xda
     const double *p = ph->params;
     d->c1 = p[0] + p[1] * sin(TWO_PI * x1) * sin(TWO_PI * x2);
     d->c2 = p[2] + p[3] * cos(TWO_PI * x1) * cos(TWO_PI * x2);
+  } else if (ph->kind == 3) {
+    const double *p = ph->params;
+    d->c1 = p[1] * (p[0] + sin(2 * TWO_PI * x1)) * (p[0] + sin(2 * TWO_PI * x2));
+    d->c2 = p[3] * (p[2] + cos(2 * TWO_PI * x1)) * (p[2] + cos(2 * TWO_PI * x2));
   } else if (ph->kind == 2 && grouped) {
     /* tau(x,theta) = Re sum_m C_m(x) exp(i m theta) with
      * C_m(x) = sum_{j : m_j = m} a_j exp(i (2 pi k_j.x + p_j)); an exact
@@ -203,6 +211,7 @@ static double psi(const or_phase *ph, const xdata *d, double x1, double x2, int 
     case 0:
       return -(p[0] * k1 + p[1] * k2) + p[2] * r;
     case 1:
+    case 3:
       return sqrt(d->c1 * d->c1 * (double)k1 * k1 + d->c2 * d->c2 * (double)k2 * k2);
     case 2:
       if (d->grouped) return r * tau_grouped(d, (k1 + I * k2) / r);

@@ -29,7 +29,7 @@ _lock = threading.Lock()
 _lib = None
 
 # phase kinds of fio_oracle.c
-SHIFT_WAVE, ELLIPSE, TAU_MODES = 0, 1, 2
+SHIFT_WAVE, ELLIPSE, TAU_MODES, ELLIPSE_PRODUCT = 0, 1, 2, 3
 AMP_ONE, AMP_SEPARABLE, AMP_HANKEL = 0, 1, 2
 
 

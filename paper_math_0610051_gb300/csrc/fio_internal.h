@@ -179,8 +179,9 @@ void release_timing_events(fio_plan_s *p);
 
 // plan_kernels.cu (FP64 plan construction on the device)
 struct PhaseDev {
-  int kind;
+  int kind;          // FIO_PHASE_ELLIPSE_PRODUCT is carried as FIO_PHASE_ELLIPSE, ell_form = 1
   int nmodes;
+  int ell_form;      // ellipse axes: 0 A + B sin sin / cos cos, 1 product form
   double p[8];       // scalar parameters (shift/wave, ellipse)
   int amp_kind;
   double a1, a2;

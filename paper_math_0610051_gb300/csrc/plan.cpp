@@ -410,11 +410,13 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   // ---- validation
   if (N < 8 || N > 2048 || (N & 1)) { set_error("N must be even, 8 <= N <= 2048"); return FIO_EINVAL; }
   if (!(eps >= 1e-12 && eps <= 0.1)) { set_error("eps must lie in [1e-12, 0.1]"); return FIO_EINVAL; }
-  if (!phase || phase->kind < 0 || phase->kind > 2 || !phase->params) {
+  if (!phase || phase->kind < 0 || phase->kind > 3 || !phase->params) {
     set_error("invalid phase descriptor");
     return FIO_EINVAL;
   }
-  const int nscal = phase->kind == FIO_PHASE_SHIFT_WAVE ? 3 : phase->kind == FIO_PHASE_ELLIPSE ? 4 : 0;
+  const int nscal = phase->kind == FIO_PHASE_SHIFT_WAVE ? 3
+                    : (phase->kind == FIO_PHASE_ELLIPSE || phase->kind == FIO_PHASE_ELLIPSE_PRODUCT) ? 4
+                                                                                                      : 0;
   if (phase->kind == FIO_PHASE_TAU_MODES) {
     if (phase->nmodes < 1 || phase->nmodes > 65536) { set_error("nmodes out of range"); return FIO_EINVAL; }
     if (!finite_all(phase->params, 5 * phase->nmodes)) { set_error("non-finite phase parameter"); return FIO_EINVAL; }
@@ -519,7 +521,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   // ---- phase data on the device
   DevAllocs tmp;
   PhaseDev ph{};
-  ph.kind = phase->kind;
+  ph.kind = phase->kind == FIO_PHASE_ELLIPSE_PRODUCT ? FIO_PHASE_ELLIPSE : phase->kind;
+  ph.ell_form = phase->kind == FIO_PHASE_ELLIPSE_PRODUCT ? 1 : 0;
   ph.nmodes = phase->kind == FIO_PHASE_TAU_MODES ? phase->nmodes : 0;
   for (int i = 0; i < nscal; ++i) ph.p[i] = phase->params[i];
   ph.amp_kind = amp1.kind;

@@ -163,8 +163,13 @@ __global__ void k_xdata(PhaseDev ph, const double *__restrict__ modes, int N, vo
   const double x1 = (double)(x / N) / N, x2 = (double)(x % N) / N;
   if (ph.kind == FIO_PHASE_ELLIPSE) {
     double2 c;
-    c.x = ph.p[0] + ph.p[1] * sinpi(2.0 * x1) * sinpi(2.0 * x2);
-    c.y = ph.p[2] + ph.p[3] * cospi(2.0 * x1) * cospi(2.0 * x2);
+    if (ph.ell_form == 1) {  // product-form axes of Eq. nrphase's experiments
+      c.x = ph.p[1] * (ph.p[0] + sinpi(4.0 * x1)) * (ph.p[0] + sinpi(4.0 * x2));
+      c.y = ph.p[3] * (ph.p[2] + cospi(4.0 * x1)) * (ph.p[2] + cospi(4.0 * x2));
+    } else {
+      c.x = ph.p[0] + ph.p[1] * sinpi(2.0 * x1) * sinpi(2.0 * x2);
+      c.y = ph.p[2] + ph.p[3] * cospi(2.0 * x1) * cospi(2.0 * x2);
+    }
     ((double2 *)xd)[x] = c;
   } else if (ph.kind == FIO_PHASE_TAU_MODES) {
     double2 C[kNm];

@@ -16,7 +16,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "_lib", "libfio.so")
 
 FIO_OK, FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ERANK, FIO_ETIMEOUT, FIO_EUNSUPPORTED = range(7)
-PHASE_SHIFT_WAVE, PHASE_ELLIPSE, PHASE_TAU_MODES = 0, 1, 2
+PHASE_SHIFT_WAVE, PHASE_ELLIPSE, PHASE_TAU_MODES, PHASE_ELLIPSE_PRODUCT = 0, 1, 2, 3
 AMP_ONE, AMP_SEPARABLE, AMP_HANKEL = 0, 1, 2
 MIXED, FP64 = 0, 1
 
@@ -163,7 +163,8 @@ class Plan:
     """fio_plan_create / fio_apply / fio_apply_adjoint for one operator L.
 
     phase: one of PHASE_* with ``params`` (shift/wave: [x01, x02, c]; ellipse:
-    [A1, B1, A2, B2]; tau modes: [K, 5] rows {a, k1, k2, m, p}).
+    [A1, B1, A2, B2]; tau modes: [K, 5] rows {a, k1, k2, m, p}; ellipse with
+    product-form axes: [a1, s1, a2, s2]).
     amp: None (a = 1), (a1, a2) for a = (1 + a1 sin 2 pi x1)(1 + a2 cos theta), or
     ("hankel", s) for the Hankel amplitude of integration along ellipses (s = +1 or -1).
     """

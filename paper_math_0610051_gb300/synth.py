@@ -113,3 +113,10 @@ def circle_grt_modes(sign: int = 1) -> np.ndarray:
     m = np.array(rows, dtype=np.float64)
     m[:, 0] *= sign
     return m
+
+
+def paper_ellipse_params() -> np.ndarray:
+    """{a1, s1, a2, s2} of the product-form ellipse phase of the paper's own
+    separation experiments (Sec. 4, Eq. nrphase): r1 = (2 + sin 4 pi x1)(2 + sin 4 pi x2)/9,
+    r2 = (2 + cos 4 pi x1)(2 + cos 4 pi x2)/9."""
+    return np.array([2.0, 1.0 / 9.0, 2.0, 1.0 / 9.0])

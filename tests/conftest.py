@@ -11,6 +11,9 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (GB300, sm_103a)")
     config.addinivalue_line("markers", "slow: takes more than a few seconds on the CPU")
+    config.addinivalue_line(
+        "markers", "gpu_long: needs a GB300 and many minutes; opt in with -m gpu_long "
+        "(not part of -m gpu)")
 
 
 @pytest.fixture(scope="session")

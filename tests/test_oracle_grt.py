@@ -48,3 +48,22 @@ def test_hankel_amplitude_envelope(orc):
     env = np.sqrt(2 / (np.pi * 2 * np.pi * rho)) / (4 * np.pi)
     assert np.all(np.abs(np.abs(ap) / env - 1) < 2e-3)
     assert np.allclose(am, np.conj(ap), rtol=0, atol=1e-15)
+
+
+def test_paper_ellipse_phase_hand_values(orc):
+    """Eq. nrphase with the axes of the paper's experiments (Sec. 4):
+    r1 = (2 + sin 4 pi x1)(2 + sin 4 pi x2)/9, r2 = (2 + cos 4 pi x1)(2 + cos 4 pi x2)/9.
+    At x = (0, 0): r1 = 4/9, r2 = 1, so Phi(x, (9, 4)) = sqrt(16 + 16).
+    At x = (1/8, 1/8): r1 = 1, r2 = 4/9, so Phi(x, (4, 9)) = 13/8 + sqrt(16 + 16).
+    At x = (1/4, 0): r1 = 4/9, r2 = 1/3, so Phi(x, (9, 3)) = 9/4 + sqrt(16 + 1)."""
+    ph = orc.Phase(orc.ELLIPSE_PRODUCT, synth.paper_ellipse_params())
+    got = orc.phase_eval(ph, [0.0, 0.125, 0.25], [0.0, 0.125, 0.0], [9, 4, 9], [4, 9, 3])
+    want = [np.sqrt(32.0), 13 / 8 + np.sqrt(32.0), 9 / 4 + np.sqrt(17.0)]
+    assert np.max(np.abs(got - want)) < 1e-13
+    # homogeneity of degree 1 in xi
+    g = np.random.default_rng(3)
+    x1, x2 = g.uniform(0, 1, 20), g.uniform(0, 1, 20)
+    k1, k2 = g.integers(-30, 31, 20), g.integers(-30, 31, 20)
+    a = orc.phase_eval(ph, x1, x2, k1, k2)
+    b = orc.phase_eval(ph, x1, x2, 3 * k1, 3 * k2)
+    assert np.max(np.abs(b - 3 * a)) < 1e-11
