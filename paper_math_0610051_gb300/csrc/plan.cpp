@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <limits>
 #include <chrono>
 #include <cmath>
 #include <complex>
@@ -222,65 +223,148 @@ static uint64_t mix_seed(uint64_t seed, uint64_t a, uint64_t b) {
 
 // ---------------------------------------------------------- eigensolver ----
 
-// Cyclic Jacobi for a Hermitian n x n matrix A (row-major); eigenvalues in
+// Eigen-decomposition of a Hermitian n x n matrix A (row-major): eigenvalues in
 // descending order, eigenvectors as the columns of V (row-major).
+//  1. Householder reduction A = Q T Q^H, T Hermitian tridiagonal: reflector k
+//     H = I - u u^H maps column k below the diagonal onto alpha e1, with
+//     alpha = -phase(x0) |x| (no cancellation in x0 - alpha).
+//  2. T' = D^H T D with a unitary diagonal D makes the off-diagonal real and
+//     non-negative: T' is real symmetric tridiagonal.
+//  3. T' = W diag(lambda) W^T by implicit symmetric QR steps with Wilkinson
+//     shifts (Golub and Van Loan, Algorithm 8.3.2): a Givens rotation chases the
+//     bulge down the unreduced block; converged off-diagonals are deflated.
+//  4. The eigenvectors of A are the columns of Q D W.
 void herm_eig(int n, std::vector<cd> A, std::vector<double> &ev, std::vector<cd> &V) {
-  V.assign((size_t)n * n, cd(0));
-  for (int i = 0; i < n; ++i) V[(size_t)i * n + i] = 1.0;
   auto at = [&](int i, int j) -> cd & { return A[(size_t)i * n + j]; };
-  double diag = 0;
-  for (int i = 0; i < n; ++i) diag += std::norm(at(i, i));
-  for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0;
-    for (int i = 0; i < n; ++i)
-      for (int j = i + 1; j < n; ++j) off += std::norm(at(i, j));
-    if (off <= 1e-32 * std::max(diag, 1e-300)) break;
-    for (int p = 0; p < n; ++p)
-      for (int q = p + 1; q < n; ++q) {
-        const cd b = at(p, q);
-        const double ab = std::abs(b);
-        if (ab == 0.0) continue;
-        const double app = at(p, p).real(), aqq = at(q, q).real();
-        if (ab < 1e-300 || (std::abs(app) + ab == std::abs(app) && std::abs(aqq) + ab == std::abs(aqq) &&
-                            sweep > 4)) {
-          at(p, q) = 0; at(q, p) = 0;
-          continue;
-        }
-        const cd e = b / ab;
-        const double tau = (aqq - app) / (2.0 * ab);
-        const double t = (tau >= 0 ? 1.0 : -1.0) / (std::abs(tau) + std::sqrt(1.0 + tau * tau));
-        const double c = 1.0 / std::sqrt(1.0 + t * t), s = t * c;
-        // U = [[c, s], [-s conj(e), c conj(e)]] on (p, q); A <- U^H A U, V <- V U
-        const cd upq = s, uqp = -s * std::conj(e), uqq = c * std::conj(e);
-        for (int k = 0; k < n; ++k) {  // columns
-          const cd akp = at(k, p), akq = at(k, q);
-          at(k, p) = akp * c + akq * uqp;
-          at(k, q) = akp * upq + akq * uqq;
-          const cd vkp = V[(size_t)k * n + p], vkq = V[(size_t)k * n + q];
-          V[(size_t)k * n + p] = vkp * c + vkq * uqp;
-          V[(size_t)k * n + q] = vkp * upq + vkq * uqq;
-        }
-        for (int k = 0; k < n; ++k) {  // rows
-          const cd apk = at(p, k), aqk = at(q, k);
-          at(p, k) = c * apk + std::conj(uqp) * aqk;
-          at(q, k) = std::conj(upq) * apk + std::conj(uqq) * aqk;
-        }
-        at(p, q) = 0;
-        at(q, p) = 0;
-        at(p, p) = at(p, p).real();
-        at(q, q) = at(q, q).real();
-      }
+  std::vector<cd> U((size_t)n * n, cd(0));  // reflector k in row k, entries k+1 .. n-1
+  std::vector<char> has(n, 0);
+  std::vector<cd> pv(n), wv(n);
+  for (int k = 0; k + 2 < n; ++k) {
+    double sig2 = 0;
+    for (int i = k + 1; i < n; ++i) sig2 += std::norm(at(i, k));
+    const double sigma = std::sqrt(sig2);
+    if (sigma == 0.0) continue;
+    const cd x0 = at(k + 1, k);
+    const double ax0 = std::abs(x0);
+    const cd phase = ax0 > 0 ? x0 / ax0 : cd(1.0);
+    const cd alpha = -phase * sigma;
+    // u = v sqrt(2 / v^H v), v = x - alpha e1, v^H v = 2 sigma (sigma + |x0|)
+    const double scale = 1.0 / std::sqrt(sigma * (sigma + ax0));
+    cd *u = &U[(size_t)k * n];
+    u[k + 1] = (x0 - alpha) * scale;
+    for (int i = k + 2; i < n; ++i) u[i] = at(i, k) * scale;
+    has[k] = 1;
+    // B = A[k+1.., k+1..] <- H B H = B - u w^H - w u^H, p = B u, w = p - (u^H p / 2) u
+    double K = 0;
+    for (int i = k + 1; i < n; ++i) {
+      cd acc = 0;
+      const cd *row = &A[(size_t)i * n];
+      for (int j = k + 1; j < n; ++j) acc += row[j] * u[j];
+      pv[i] = acc;
+      K += (std::conj(u[i]) * acc).real();
+    }
+    for (int i = k + 1; i < n; ++i) wv[i] = pv[i] - 0.5 * K * u[i];
+    for (int i = k + 1; i < n; ++i) {
+      cd *row = &A[(size_t)i * n];
+      const cd ui = u[i], wi = wv[i];
+      for (int j = k + 1; j < n; ++j) row[j] -= ui * std::conj(wv[j]) + wi * std::conj(u[j]);
+    }
+    at(k + 1, k) = alpha;
+    at(k, k + 1) = std::conj(alpha);
+    for (int i = k + 2; i < n; ++i) at(i, k) = at(k, i) = 0;
   }
+  // Q = H_0 H_1 ... H_{n-3}, accumulated from the last reflector
+  std::vector<cd> Q((size_t)n * n, cd(0));
+  for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
+  std::vector<cd> yv(n);
+  for (int k = n - 3; k >= 0; --k) {
+    if (!has[k]) continue;
+    const cd *u = &U[(size_t)k * n];
+    std::fill(yv.begin(), yv.end(), cd(0));
+    for (int i = k + 1; i < n; ++i) {
+      const cd cu = std::conj(u[i]);
+      const cd *row = &Q[(size_t)i * n];
+      for (int j = k + 1; j < n; ++j) yv[j] += cu * row[j];
+    }
+    for (int i = k + 1; i < n; ++i) {
+      cd *row = &Q[(size_t)i * n];
+      const cd ui = u[i];
+      for (int j = k + 1; j < n; ++j) row[j] -= ui * yv[j];
+    }
+  }
+  // real symmetric tridiagonal d, e (e[k] couples k and k+1) and the phases D
+  std::vector<double> d(n), e(std::max(n - 1, 0));
+  std::vector<cd> D(n, cd(1.0));
+  for (int k = 0; k < n; ++k) d[k] = at(k, k).real();
+  for (int k = 0; k + 1 < n; ++k) {
+    const cd b = at(k + 1, k);
+    const double ab = std::abs(b);
+    e[k] = ab;
+    D[k + 1] = ab > 0 ? D[k] * (b / ab) : D[k];
+  }
+  // implicit symmetric QR on d, e; W accumulates the rotations (real, row-major)
+  std::vector<double> W((size_t)n * n, 0.0);
+  for (int i = 0; i < n; ++i) W[(size_t)i * n + i] = 1.0;
+  const double tol = 4.0 * std::numeric_limits<double>::epsilon();
+  int hi = n - 1;
+  long long steps = 0;
+  while (hi > 0 && steps < 60LL * n) {
+    if (std::abs(e[hi - 1]) <= tol * (std::abs(d[hi - 1]) + std::abs(d[hi]))) {
+      e[hi - 1] = 0.0;
+      --hi;
+      continue;
+    }
+    int lo = hi - 1;
+    while (lo > 0 && std::abs(e[lo - 1]) > tol * (std::abs(d[lo - 1]) + std::abs(d[lo]))) --lo;
+    ++steps;
+    // Wilkinson shift from the trailing 2 x 2 of the block
+    const double t = 0.5 * (d[hi - 1] - d[hi]), b2 = e[hi - 1] * e[hi - 1];
+    const double mu = d[hi] - b2 / (t + (t >= 0 ? 1.0 : -1.0) * std::sqrt(t * t + b2));
+    double x = d[lo] - mu, z = e[lo];
+    for (int k = lo; k < hi; ++k) {
+      // P = [[c, s], [-s, c]] on (k, k+1): P^T [x; z] = [r; 0]
+      const double r = std::hypot(x, z);
+      const double c = r > 0 ? x / r : 1.0, s = r > 0 ? -z / r : 0.0;
+      if (k > lo) e[k - 1] = r;  // the bulge at (k+1, k-1) is gone
+      const double a = d[k], bb = e[k], cc = d[k + 1];
+      d[k] = a * c * c - 2.0 * bb * c * s + cc * s * s;
+      d[k + 1] = a * s * s + 2.0 * bb * c * s + cc * c * c;
+      e[k] = (a - cc) * c * s + bb * (c * c - s * s);
+      if (k + 1 < hi) {
+        const double f = e[k + 1];
+        z = -s * f;  // new bulge at (k+2, k)
+        e[k + 1] = c * f;
+        x = e[k];
+      }
+      for (int i = 0; i < n; ++i) {
+        double *wr = &W[(size_t)i * n];
+        const double wk = wr[k], wk1 = wr[k + 1];
+        wr[k] = c * wk - s * wk1;
+        wr[k + 1] = s * wk + c * wk1;
+      }
+    }
+  }
+  // V = Q D W, columns sorted by descending eigenvalue
   std::vector<int> idx(n);
   std::iota(idx.begin(), idx.end(), 0);
-  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return at(a, a).real() > at(b, b).real(); });
-  ev.resize(n);
-  std::vector<cd> Vs((size_t)n * n);
-  for (int j = 0; j < n; ++j) {
-    ev[j] = at(idx[j], idx[j]).real();
-    for (int i = 0; i < n; ++i) Vs[(size_t)i * n + j] = V[(size_t)i * n + idx[j]];
+  std::sort(idx.begin(), idx.end(), [&](int a, int b) { return d[a] > d[b]; });
+  std::vector<cd> QD((size_t)n * n);
+  for (int i = 0; i < n; ++i)
+    for (int k = 0; k < n; ++k) QD[(size_t)i * n + k] = Q[(size_t)i * n + k] * D[k];
+  std::vector<double> Ws((size_t)n * n);
+  for (int k = 0; k < n; ++k)
+    for (int j = 0; j < n; ++j) Ws[(size_t)k * n + j] = W[(size_t)k * n + idx[j]];
+  V.assign((size_t)n * n, cd(0));
+  for (int i = 0; i < n; ++i) {
+    cd *vr = &V[(size_t)i * n];
+    for (int k = 0; k < n; ++k) {
+      const cd q = QD[(size_t)i * n + k];
+      const double *wr = &Ws[(size_t)k * n];
+      for (int j = 0; j < n; ++j) vr[j] += q * wr[j];
+    }
   }
-  V.swap(Vs);
+  ev.resize(n);
+  for (int j = 0; j < n; ++j) ev[j] = d[idx[j]];
 }
 
 // ------------------------------------------------------ device bookkeeping --
