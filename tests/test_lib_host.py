@@ -166,6 +166,39 @@ def test_host_eigh_rank_deficient(fio):
     assert np.max(np.abs(A @ V[:, :3] - V[:, :3] * ev[:3])) < 1e-10 * ev[0]
 
 
+@pytest.mark.parametrize("case", ["plan_gram", "clusters", "diagonal", "zero", "tiny"])
+def test_host_eigh_structured(fio, case):
+    """Matrices of the kinds the separation meets: Gram matrices of unit-modulus
+    phase columns (A_[C]^H A_[C]), two tight eigenvalue clusters, an already
+    diagonal matrix, the zero matrix and the 1 x 1 and 2 x 2 cases."""
+    g = np.random.default_rng(11)
+    if case == "plan_gram":
+        x = g.uniform(0, 1, (300, 1))
+        k = g.uniform(-40, 40, (1, 96))
+        Am = np.exp(2j * np.pi * (x * k + 0.3 * np.sin(2 * np.pi * x) * np.abs(k)))
+        mats = [Am.conj().T @ Am]
+    elif case == "clusters":
+        X = g.standard_normal((120, 120)) + 1j * g.standard_normal((120, 120))
+        Q, _ = np.linalg.qr(X)
+        lam = np.concatenate([np.ones(60), 1e-9 * np.ones(60)])
+        mats = [(Q * lam) @ Q.conj().T]
+    elif case == "diagonal":
+        mats = [np.diag(np.arange(16.0)).astype(complex)]
+    elif case == "zero":
+        mats = [np.zeros((7, 7), complex)]
+    else:
+        mats = [np.array([[2.5]], complex), np.array([[1.0, 2 - 1j], [2 + 1j, -3.0]])]
+    for A in mats:
+        n = A.shape[0]
+        ev, V = fio.host_eigh(A)
+        ref = np.sort(np.linalg.eigvalsh(A))[::-1]
+        scale = max(np.max(np.abs(ref)), 1e-300)
+        assert np.all(np.diff(ev) <= 1e-12 * scale)          # descending
+        assert np.max(np.abs(ev - ref)) < 1e-12 * scale
+        assert np.max(np.abs(V.conj().T @ V - np.eye(n))) < 1e-11
+        assert np.max(np.abs(A @ V - V * ev)) < 1e-11 * scale + 1e-300
+
+
 def test_plan_create_rejects_bad_arguments_before_cuda(fio):
     """Argument errors are reported before any CUDA call (FIO_EINVAL), with a message."""
     lib = fio.lib()
