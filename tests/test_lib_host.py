@@ -219,4 +219,26 @@ def test_plan_create_rejects_bad_arguments_before_cuda(fio):
     assert b"non-finite" in lib.fio_last_error()
     assert create(64, tau.ravel().copy(), fio.PHASE_TAU_MODES, nmodes=1)[0] == fio.FIO_EINVAL
     assert lib.fio_apply(None, None, None, 1, None) == fio.FIO_EINVAL
+    assert lib.fio_apply_normal(None, None, None, 1, None) == fio.FIO_EINVAL
     assert lib.fio_dft2(100 + 14, 0, None, None, 1, 0, None) == fio.FIO_EINVAL
+    # phase kinds: unknown kind, and a non-finite product-form ellipse parameter
+    assert create(64, prm, kind=4)[0] == fio.FIO_EINVAL
+    assert create(64, bad, kind=fio.PHASE_ELLIPSE_PRODUCT)[0] == fio.FIO_EINVAL
+
+
+def test_hankel_amplitude_sign_is_validated(fio):
+    """FIO_AMP_HANKEL takes its sign from a1, which must be +1 or -1."""
+    lib = fio.lib()
+    prm = np.ascontiguousarray(fio_synth().circle_grt_modes(1).ravel())
+    ph = fio._Phase(fio.PHASE_TAU_MODES, 5, prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+    for a1 in (0.5, 0.0, 2.0, np.nan):
+        am = fio._Amp(fio.AMP_HANKEL, a1, 0.0)
+        h = ctypes.c_void_p()
+        st = lib.fio_plan_create(64, ctypes.byref(ph), ctypes.byref(am), 1e-4, None, ctypes.byref(h))
+        assert (st, h.value) == (fio.FIO_EINVAL, None), a1
+        assert b"amplitude" in lib.fio_last_error()
+
+
+def fio_synth():
+    from paper_math_0610051_gb300 import synth
+    return synth
