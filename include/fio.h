@@ -176,7 +176,9 @@ fio_status fio_apply_normal(fio_plan plan, const void *f, void *out, int batch, 
  *   - Set-up: the first call on a device looks up the scratch array's device
  *     address (cudaGetSymbolAddress) with that device current, and the plan's
  *     device must be the current device.  Make that first call before any
- *     stream capture.
+ *     stream capture.  The address is kept for the life of the process: after
+ *     cudaDeviceReset (which also destroys every plan on that device) no call
+ *     may follow.
  *   - Sharing: every call uses the same array, which keeps the last call's
  *     contents.  The forward path writes every scratch value before reading it,
  *     so nothing has to be cleared, but two calls that may overlap on the GPU

@@ -67,3 +67,33 @@ def test_paper_ellipse_phase_hand_values(orc):
     a = orc.phase_eval(ph, x1, x2, k1, k2)
     b = orc.phase_eval(ph, x1, x2, 3 * k1, 3 * k2)
     assert np.max(np.abs(b - 3 * a)) < 1e-11
+
+
+def test_hankel_amplitude_is_the_hankel_function(orc):
+    """Appendix A, Eq. ellipses_amp: a+ = H0^(1)(2 pi rho) e^{-2 pi i rho} / (4 pi) and
+    a- = H0^(2)(2 pi rho) e^{+2 pi i rho} / (4 pi), since J0 + i Y0 = H0^(1) and
+    J0 - i Y0 = H0^(2).  scipy's Hankel functions are an independent evaluation, and a
+    flipped sign of the Y0 term (H0^(2) in a+) fails this at every rho."""
+    rho = np.array([0.1, 0.37, 1.0, 2.5, 7.3, 31.0, 120.0])
+    z = 2 * np.pi * rho
+    zeros, ones = np.zeros(len(rho)), [1] * len(rho)
+    ap = orc.amp_eval(orc.Amplitude(orc.AMP_HANKEL, 1), zeros, ones, [0] * len(rho), rho)
+    am = orc.amp_eval(orc.Amplitude(orc.AMP_HANKEL, -1), zeros, ones, [0] * len(rho), -rho)
+    want_p = sp.hankel1(0, z) * np.exp(-1j * z) / (4 * np.pi)
+    want_m = sp.hankel2(0, z) * np.exp(1j * z) / (4 * np.pi)
+    assert np.max(np.abs(ap - want_p) / np.abs(want_p)) < 1e-13
+    assert np.max(np.abs(am - want_m) / np.abs(want_m)) < 1e-13
+
+
+def test_hankel_amplitude_is_demodulated(orc):
+    """The point of Appendix A's split: a+ is the smooth envelope of the outgoing wave,
+    H0^(1)(z) ~ sqrt(2 / (pi z)) e^{i (z - pi/4)}, so arg a+ -> -pi/4 and arg a- -> +pi/4
+    as rho grows (with the sign flipped, a+ would oscillate like e^{-2 i z})."""
+    rho = np.array([40.0, 160.0, 640.0, 2560.0])
+    n = len(rho)
+    ap = orc.amp_eval(orc.Amplitude(orc.AMP_HANKEL, 1), np.zeros(n), [1] * n, [0] * n, rho)
+    am = orc.amp_eval(orc.Amplitude(orc.AMP_HANKEL, -1), np.zeros(n), [1] * n, [0] * n, -rho)
+    # next term of the expansion: the phase error is about 1 / (8 z)
+    tol = 1.0 / (8 * 2 * np.pi * rho) * 1.5
+    assert np.all(np.abs(np.angle(ap) + np.pi / 4) < tol)
+    assert np.all(np.abs(np.angle(am) - np.pi / 4) < tol)

@@ -78,3 +78,43 @@ def test_tau_matches_phase(orc):
     phi = orc.phase_eval(orc.Phase(orc.TAU_MODES, modes), x1, x2, k1, k2)
     tau = orc.tau_eval(modes, x1, x2, np.arctan2(k2, k1))[:, 0]
     assert np.max(np.abs(phi - (x1 * k1 + x2 * k2) - np.hypot(k1, k2) * tau)) < 1e-11
+
+
+def test_mlp_forward_hand_value():
+    """A worked value of the 4 -> 64 -> 64 -> 3 tanh network with one non-zero weight per
+    layer, reached at points where tanh(z) differs from z (a dropped activation, a
+    missing input map 2x - 1 or a transposed weight index fails it).
+    Input x = (0.75, 0.25, cos t, sin t) -> first-layer input (0.5, -0.5, cos t, sin t).
+      h1[5]  = tanh(1.5 * 0.5 + 0.2)           (W1[0][5] = 1.5, b1[5] = 0.2)
+      h2[7]  = tanh(-2.0 * h1[5] + 0.1)        (W2[5][7] = -2.0, b2[7] = 0.1)
+      y      = (0.3, 0.7 h2[7] - 0.4, 0)       (W3[7][1] = 0.7, b3 = (0.3, -0.4, 0))
+    Every other unit is tanh(0) = 0 and adds nothing."""
+    W1, b1, W2, b2, W3, b3 = [np.zeros(s) for s in mlp.SIZES]
+    W1[0, 5], b1[5] = 1.5, 0.2
+    W2[5, 7], b2[7] = -2.0, 0.1
+    W3[7, 1] = 0.7
+    b3[:] = [0.3, -0.4, 0.0]
+    p = np.concatenate([a.ravel() for a in (W1, b1, W2, b2, W3, b3)])
+    X = np.array([[0.75, 0.25, np.cos(0.3), np.sin(0.3)]])
+    h1 = np.tanh(1.5 * 0.5 + 0.2)
+    h2 = np.tanh(-2.0 * h1 + 0.1)
+    y, _ = mlp.forward(p, X)
+    assert np.allclose(y[0], [0.3, 0.7 * h2 - 0.4, 0.0], rtol=0, atol=1e-15)
+    # the numbers themselves (tanh 0.95 = 0.739783..., tanh(-1.379566) = -0.880854...)
+    assert abs(y[0, 1] - (0.7 * -0.88085407 - 0.4)) < 1e-7
+    # d y / d theta: the angular inputs carry no weight here, so it vanishes
+    assert abs(mlp.dtheta(p, X)[0]) < 1e-15
+
+
+def test_mlp_dtheta_hand_value():
+    """An angular weight: W1[3][0] = 1 (sin t -> unit 0), W2[0][0] = 1, W3[0][0] = 1:
+    y0 = tanh(tanh(sin t)), so d y0 / d t = (1 - y0^2)(1 - tanh(sin t)^2) cos t."""
+    W1, b1, W2, b2, W3, b3 = [np.zeros(s) for s in mlp.SIZES]
+    W1[3, 0] = W2[0, 0] = W3[0, 0] = 1.0
+    p = np.concatenate([a.ravel() for a in (W1, b1, W2, b2, W3, b3)])
+    t = 1.1
+    X = np.array([[0.1, 0.9, np.cos(t), np.sin(t)]])
+    u = np.tanh(np.sin(t))
+    y0 = np.tanh(u)
+    assert abs(mlp.forward(p, X)[0][0, 0] - y0) < 1e-15
+    assert abs(mlp.dtheta(p, X)[0] - (1 - y0 ** 2) * (1 - u ** 2) * np.cos(t)) < 1e-15

@@ -68,3 +68,28 @@ def test_noalloc_rejects_oversize(env):
         out = torch.empty_like(f)
         assert _noalloc(fio, torch, plan, f, out) == fio.FIO_EINVAL
         assert b"FIO_NOALLOC_SCRATCH_BYTES" in fio.lib().fio_last_error()
+
+
+def test_noalloc_batch_beyond_max_batch_allocates_nothing(env):
+    """The entry's batch is bounded by the scratch array, not by the plan's
+    max_batch: a plan made for one input applies four in one call, equal to four
+    single fio_apply calls.  After a first call, further calls leave the device's
+    free memory unchanged."""
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    N, B = 64, 4
+    with fio.Plan(N, fio.PHASE_ELLIPSE, synth.ellipse_params(), 1e-4, max_batch=1) as plan:
+        f = torch.from_numpy(synth.white_noise(N, B, seed=3, real=False)).to(torch.complex64).cuda()
+        ref = torch.stack([plan.apply(f[b:b + 1])[0] for b in range(B)])
+        out = torch.empty_like(f)
+        assert _noalloc(fio, torch, plan, f, out) == fio.FIO_OK  # set-up call
+        torch.cuda.synchronize()
+        free0 = torch.cuda.mem_get_info()[0]
+        for _ in range(2):
+            out.fill_(float("nan"))
+            assert _noalloc(fio, torch, plan, f, out) == fio.FIO_OK
+            torch.cuda.synchronize()
+            assert torch.cuda.mem_get_info()[0] == free0
+            err = (torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref)).item()
+            assert err <= 1e-6, err
+        plan.sync()
