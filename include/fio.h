@@ -110,6 +110,10 @@ typedef struct {
   fio_surrogate surrogate;    /* trained phase surrogate (tau-mode phases), or NULL; see below */
   double surrogate_warp_budget; /* largest judged warp error, in cycles at |xi| = N/sqrt 2, for
                                    which the surrogate's warped points are used; 0 = 0.5 */
+  double sep_cut;             /* singular values of A_[C] above sep_cut * eps * s_1 are kept
+                                 (Sec. 3.2 step 2); 0 = 0.25, at most 1 */
+  double sep_target;          /* a sample is accepted when the validated separation error is
+                                 at most sep_target * eps and q <= r/3; 0 = 0.5, at most 1 */
 } fio_options;
 
 /* Fill *opt with the defaults listed above.  Returns FIO_EINVAL for NULL. */
@@ -361,10 +365,21 @@ fio_status fio_kb_eval(int w, double beta, int n, const double *s, double *phi, 
 int fio_kb_width_for(double eps);
 
 /* Eigendecomposition of a Hermitian n x n complex matrix (host, row-major,
- * interleaved re/im, n <= 1024) by cyclic Jacobi rotations: evals descending,
- * V's columns the eigenvectors (row-major interleaved).  This is the solver the
- * randomized separation uses for the Gram matrix of the sampled columns. */
+ * interleaved re/im, n <= 1024) by Householder tridiagonalisation and implicit
+ * symmetric QR steps with Wilkinson shifts: evals descending, V's columns the
+ * eigenvectors (row-major interleaved).  A host utility; the randomized
+ * separation does not form Gram matrices (see fio_host_svd). */
 fio_status fio_host_eigh(int n, const double *A, double *evals, double *V);
+
+/* Singular value decomposition of an m x n complex matrix (host, row-major,
+ * interleaved re/im; 1 <= m <= 1 << 20, 1 <= n <= 1024) by one-sided Jacobi
+ * rotations: s (n values, descending), AV = A V (m x n; column j is s_j times
+ * the j-th left singular vector, or a zero column where s_j = 0) and V (n x n,
+ * columns the right singular vectors).  The randomized separation (Sec. 3.2)
+ * applies it to the triangular factor of A_[C] = Q R and to U_[R]; small
+ * singular values keep an absolute accuracy of about 1e-16 s_1.  Any output
+ * pointer may be NULL. */
+fio_status fio_host_svd(int m, int n, const double *A, double *s, double *AV, double *V);
 
 const char *fio_status_string(fio_status s);
 const char *fio_last_error(void);

@@ -23,7 +23,7 @@ NVCC = os.path.join(CUDA_HOME, "bin", "nvcc")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 NVCC_FLAGS = ARCH + ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC",
                      "-I" + os.path.join(ROOT, "include")]
-CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-I" + os.path.join(CUDA_HOME, "include"),
+CXX_FLAGS = ["-O2", "-std=c++17", "-fPIC", "-fopenmp", "-I" + os.path.join(CUDA_HOME, "include"),
              "-I" + os.path.join(ROOT, "include")]
 
 
@@ -70,7 +70,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     if force or not os.path.exists(LIB) or os.path.getmtime(LIB) < newest:
         tmp = LIB + f".{os.getpid()}.tmp"
         cmd = [NVCC] + ARCH + ["-shared", "-o", tmp] + objs + ["-lcudart_static", "-ldl", "-lrt",
-                                                             "-lpthread"]
+                                                             "-lpthread", "-lgomp"]
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
             raise RuntimeError(f"link failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")

@@ -435,4 +435,27 @@ fio_status fio_host_eigh(int n, const double *A, double *evals, double *V) {
   return FIO_OK;
 }
 
+fio_status fio_host_svd(int m, int n, const double *A, double *s, double *AV, double *V) {
+  if (m < 1 || m > (1 << 20) || n < 1 || n > 1024 || !A) {
+    set_error("fio_host_svd: bad arguments");
+    return FIO_EINVAL;
+  }
+  using cd = std::complex<double>;
+  std::vector<cd> M((size_t)m * n);
+  for (size_t i = 0; i < M.size(); ++i) M[i] = cd(A[2 * i], A[2 * i + 1]);
+  std::vector<double> sig;
+  std::vector<cd> Vm;
+  svd_jacobi(m, n, M, sig, Vm);
+  for (int i = 0; s && i < n; ++i) s[i] = sig[i];
+  for (size_t i = 0; AV && i < M.size(); ++i) {
+    AV[2 * i] = M[i].real();
+    AV[2 * i + 1] = M[i].imag();
+  }
+  for (size_t i = 0; V && i < Vm.size(); ++i) {
+    V[2 * i] = Vm[i].real();
+    V[2 * i + 1] = Vm[i].imag();
+  }
+  return FIO_OK;
+}
+
 }  // extern "C"

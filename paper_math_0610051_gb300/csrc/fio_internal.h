@@ -196,9 +196,15 @@ cudaError_t plan_warp(const PhaseDev &ph, const void *d_xdata, int N, int L, con
 cudaError_t plan_eval_cols(const PhaseDev &ph, const void *d_xdata, int N, const WedgeDev &w,
                            const uint2 *d_warp_l, const int *d_ck1, const int *d_ck2, int r,
                            double2 *d_AC, cudaStream_t s);
-// Gram matrix G = A_C^H A_C (r x r), deterministic two-level reduction.
-cudaError_t plan_gram(const double2 *d_AC, long long rows, int r, double2 *d_partial,
-                      int nparts, double2 *d_G, cudaStream_t s);
+// R of A = Q R (A: rows x r, row-major) by tall-skinny Householder QR: panels of
+// tsqr_panel_rows(r) rows are factored in parallel, their R factors stacked and
+// factored again until one remains; h_R (HOST, r x r row-major, zero below the
+// diagonal) receives it after the stream synchronises.  d_work holds rows * r
+// values, d_stk0 and d_stk1 tsqr_stack_elems(rows, r) each.
+int tsqr_panel_rows(int r);
+size_t tsqr_stack_elems(long long rows, int r);
+cudaError_t plan_tsqr(const double2 *d_A, long long rows, int r, double2 *d_work, double2 *d_stk0,
+                      double2 *d_stk1, double2 *h_R, cudaStream_t s);
 // alpha[pos][t] = (sum_c A_C[x][c] W[c][t]) * exp(2 pi i y'.xi_c) / N with x = perm[pos]
 // (W = V S^-1, r x q)
 cudaError_t plan_form_alpha(const double2 *d_AC, int N, int r, int q, const double2 *d_W,

@@ -1,9 +1,10 @@
 // plan.cpp -- host side of fio_plan_create: polar wedges (Sec. 1.3), the
 // shear/translate boxes and NUFFT grids (Sec. 3.4), the Kaiser-Bessel kernel,
-// and the randomized separation of Sec. 3.2 (sample columns, SVD through the
-// Gram matrix, threshold eps, double r until q <= r/3, sample rows,
-// T = U_[R]^+ A_[R]).  Large FP64 work runs in plan_kernels.cu; the r x r and
-// q x q eigenproblems run here.
+// and the randomized separation of Sec. 3.2 (sample columns, SVD of A_[C]
+// through its QR factorization, threshold eps, double r until q <= r/3, sample
+// rows, T = U_[R]^+ A_[R]).  Large FP64 work (A_[C], its tall-skinny QR, the
+// factors) runs in plan_kernels.cu; the SVDs of the r x r triangular factor and
+// of U_[R] run here by one-sided Jacobi.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -27,11 +28,12 @@ namespace fio {
 using cd = std::complex<double>;
 
 // Separation rule (Sec. 3.2 with a stricter acceptance test): singular values
-// of A_[C] above kSvdFraction * eps * s_1 are kept; a sample is accepted when
+// of A_[C] above sep_cut * eps * s_1 are kept; a sample is accepted when
 // q <= r/3 and the relative Frobenius error of U T, measured on
 // kValidationRows fresh random rows against every column of the wedge, is at
-// most kValidationTarget * eps.  Otherwise the worst-fitted columns join the
-// next sample and r doubles.
+// most sep_target * eps.  Otherwise the worst-fitted columns join the next
+// sample and r doubles.  The defaults below apply when fio_options leaves
+// them 0.
 constexpr double kSvdFraction = 0.25;
 constexpr double kValidationTarget = 0.5;
 constexpr int kValidationRows = 200;
@@ -367,6 +369,104 @@ void herm_eig(int n, std::vector<cd> A, std::vector<double> &ev, std::vector<cd>
   for (int j = 0; j < n; ++j) ev[j] = d[idx[j]];
 }
 
+// Singular value decomposition of an m x n complex matrix A (row-major) by
+// one-sided Jacobi rotations (Hestenes): unitary plane rotations J applied on
+// the right until every pair of columns of A V is orthogonal to working
+// precision.  Then A V = U diag(sig): the column norms are the singular
+// values, and V (n x n, row-major) collects the rotations.  A^H A is never
+// formed, so small singular values keep their absolute accuracy eps ||A||
+// (Demmel and Veselic, 1992).  On return A holds A V with its columns in the
+// order of sig, which is descending.
+//
+// A pair (p, q) with gamma = a_p^H a_q = |gamma| e^{i phi} is rotated by
+//   a_p <- c a_p - s e^{-i phi} a_q,   a_q <- s a_p + c e^{-i phi} a_q,
+// t = s / c the smaller root of t^2 + 2 zeta t - 1 = 0,
+// zeta = (|a_q|^2 - |a_p|^2) / (2 |gamma|), which makes the new pair orthogonal.
+void svd_jacobi(int m, int n, std::vector<cd> &A, std::vector<double> &sig, std::vector<cd> &V) {
+  std::vector<cd> Ac((size_t)m * n), Vc((size_t)n * n, cd(0));  // column-major work copies
+  for (int i = 0; i < m; ++i)
+    for (int j = 0; j < n; ++j) Ac[(size_t)j * m + i] = A[(size_t)i * n + j];
+  for (int j = 0; j < n; ++j) Vc[(size_t)j * n + j] = 1.0;
+  const double tol = std::max(1e-15, std::sqrt((double)m) * std::numeric_limits<double>::epsilon());
+  // squared column norms, refreshed by every rotation that changes a column
+  std::vector<double> nrm2(n, 0.0);
+  double fro2 = 0;
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < m; ++i) nrm2[j] += std::norm(Ac[(size_t)j * m + i]);
+    fro2 += nrm2[j];
+  }
+  // columns below 1e-18 ||A||_F are numerically zero: rotating them changes A by
+  // less than its rounding, and their tiny (even denormal) inner products would
+  // give inexact rotation phases
+  const double tiny2 = 1e-36 * fro2;
+  // round-robin ordering: each round pairs every column once, the pairs of a
+  // round are disjoint and are rotated in parallel
+  const int nn = n + (n & 1);
+  std::vector<int> perm(nn);
+  std::iota(perm.begin(), perm.end(), 0);
+  const bool par = (long long)m * n >= 4096;
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    long long rotated = 0;
+    for (int round = 0; round + 1 < nn; ++round) {
+#pragma omp parallel for reduction(+ : rotated) schedule(static) if (par)
+      for (int k = 0; k < nn / 2; ++k) {
+        int p = perm[k], q = perm[nn - 1 - k];
+        if (p >= n || q >= n) continue;
+        if (p > q) std::swap(p, q);
+        cd *ap = &Ac[(size_t)p * m], *aq = &Ac[(size_t)q * m];
+        const double al = nrm2[p], be = nrm2[q];
+        if (al <= tiny2 || be <= tiny2) continue;
+        cd ga = 0;
+        for (int i = 0; i < m; ++i) ga += std::conj(ap[i]) * aq[i];
+        const double ag = std::abs(ga);
+        if (ag <= tol * std::sqrt(al) * std::sqrt(be)) continue;
+        ++rotated;
+        const cd eph = std::conj(ga / ag);  // e^{-i phi}
+        const double zeta = (be - al) / (2.0 * ag);
+        const double t = (zeta >= 0 ? 1.0 : -1.0) / (std::abs(zeta) + std::sqrt(1.0 + zeta * zeta));
+        const double c = 1.0 / std::sqrt(1.0 + t * t), sn = c * t;
+        double np = 0, nq = 0;
+        for (int i = 0; i < m; ++i) {
+          const cd x = ap[i], y = eph * aq[i];
+          ap[i] = c * x - sn * y;
+          aq[i] = sn * x + c * y;
+          np += std::norm(ap[i]);
+          nq += std::norm(aq[i]);
+        }
+        nrm2[p] = np;
+        nrm2[q] = nq;
+        cd *vp = &Vc[(size_t)p * n], *vq = &Vc[(size_t)q * n];
+        for (int i = 0; i < n; ++i) {
+          const cd x = vp[i], y = eph * vq[i];
+          vp[i] = c * x - sn * y;
+          vq[i] = sn * x + c * y;
+        }
+      }
+      const int last = perm[nn - 1];  // keep perm[0], rotate the others one place
+      for (int i = nn - 1; i > 1; --i) perm[i] = perm[i - 1];
+      if (nn > 1) perm[1] = last;
+    }
+    if (!rotated) break;
+  }
+  std::vector<double> nrm(n);
+  for (int j = 0; j < n; ++j) {
+    double acc = 0;
+    for (int i = 0; i < m; ++i) acc += std::norm(Ac[(size_t)j * m + i]);
+    nrm[j] = std::sqrt(acc);
+  }
+  std::vector<int> idx(n);
+  std::iota(idx.begin(), idx.end(), 0);
+  std::stable_sort(idx.begin(), idx.end(), [&](int a, int b) { return nrm[a] > nrm[b]; });
+  sig.resize(n);
+  V.assign((size_t)n * n, cd(0));
+  for (int k = 0; k < n; ++k) {
+    const int j = idx[k];
+    sig[k] = nrm[j];
+    for (int i = 0; i < m; ++i) A[(size_t)i * n + k] = Ac[(size_t)j * m + i];
+    for (int i = 0; i < n; ++i) V[(size_t)i * n + k] = Vc[(size_t)j * n + i];
+  }
+}
+
 // ------------------------------------------------------ device bookkeeping --
 
 namespace {
@@ -528,6 +628,10 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   const int rank_cap = opt.rank_cap > 0 ? opt.rank_cap : 512;
   const int max_batch = opt.max_batch > 0 ? opt.max_batch : 1;
   if (max_batch > 4096) { set_error("max_batch too large"); return FIO_EINVAL; }
+  if (!(opt.sep_cut >= 0 && opt.sep_cut <= 1) || !(opt.sep_target >= 0 && opt.sep_target <= 1)) {
+    set_error("sep_cut and sep_target must lie in [0, 1] (0 = default)");
+    return FIO_EINVAL;
+  }
 
   p->N = N; p->L = L; p->eps = eps; p->sigma = sigma; p->precision = opt.precision;
   p->max_batch = max_batch;
@@ -650,12 +754,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
 
   // ---- pass 1: randomized separation rank per wedge (Sec. 3.2)
   p->wedge_r.assign(L, 0);
-  double2 *d_AC = nullptr, *d_G = nullptr, *d_part = nullptr;
-  long long ac_cap = 0, g_cap = 0, part_cap = 0;
-  auto nparts_for = [](int r) {
-    const int ntile = (r + 31) / 32;
-    return std::max(1, std::min(1024, 1024 / (ntile * (ntile + 1) / 2)));
-  };
+  double2 *d_AC = nullptr, *d_qrw = nullptr, *d_stk0 = nullptr, *d_stk1 = nullptr;
+  long long ac_cap = 0, qrw_cap = 0, stk0_cap = 0, stk1_cap = 0;
   auto regrow = [&](double2 **q, long long &cap, long long need, const char *what) -> fio_status {
     if (need <= cap) return FIO_OK;
     if (*q) {
@@ -670,9 +770,14 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     return FIO_OK;
   };
   auto ensure_ac = [&](int r) -> fio_status {
-    fio_status s = regrow(&d_AC, ac_cap, (long long)r * NN, "alloc A_C");
-    if (s == FIO_OK) s = regrow(&d_G, g_cap, (long long)r * r, "alloc G");
-    if (s == FIO_OK) s = regrow(&d_part, part_cap, (long long)nparts_for(r) * r * r, "alloc Gram partials");
+    return regrow(&d_AC, ac_cap, (long long)r * NN, "alloc A_C");
+  };
+  // workspace of the tall-skinny QR of A_C (pass 1 only)
+  auto ensure_qr = [&](int r) -> fio_status {
+    const long long st = (long long)tsqr_stack_elems(NN, r);
+    fio_status s = regrow(&d_qrw, qrw_cap, (long long)r * NN, "alloc QR workspace");
+    if (s == FIO_OK) s = regrow(&d_stk0, stk0_cap, st, "alloc QR stack");
+    if (s == FIO_OK) s = regrow(&d_stk1, stk1_cap, st, "alloc QR stack");
     return s;
   };
   int *d_ck1 = nullptr, *d_ck2 = nullptr;
@@ -738,44 +843,37 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     }
     return FIO_OK;
   };
-  // P = U_R^+ (q x nr) through the eigendecomposition of U_R^H U_R, relative cutoff
+  // P = U_R^+ (q x nr) from the SVD of U_R (one-sided Jacobi): U_R W = Y with
+  // orthogonal columns of norms s_k, so U_R^+ = W diag(1/s_k^2) Y^H over the
+  // s_k above cut * s_1 (Sec. 3.2's pseudo-inverse, without normal equations)
   auto pinv = [&](const std::vector<cd> &UR, int nr, int q, double cut) {
-    std::vector<cd> Gq((size_t)q * q, cd(0));
-    for (int a = 0; a < q; ++a)
-      for (int b = 0; b < q; ++b) {
-        cd acc = 0;
-        for (int i = 0; i < nr; ++i) acc += std::conj(UR[(size_t)i * q + a]) * UR[(size_t)i * q + b];
-        Gq[(size_t)a * q + b] = acc;
-      }
-    std::vector<double> evq;
-    std::vector<cd> Q;
-    herm_eig(q, Gq, evq, Q);
-    std::vector<cd> Ginv((size_t)q * q, cd(0));
-    for (int k = 0; k < q; ++k) {
-      if (!(evq[k] > cut * cut * evq[0])) continue;
-      for (int a = 0; a < q; ++a)
-        for (int b = 0; b < q; ++b)
-          Ginv[(size_t)a * q + b] += Q[(size_t)a * q + k] * std::conj(Q[(size_t)b * q + k]) / evq[k];
-    }
+    std::vector<cd> Y = UR, Wv;
+    std::vector<double> su;
+    svd_jacobi(nr, q, Y, su, Wv);
     std::vector<cd> P((size_t)q * nr, cd(0));
-    for (int t = 0; t < q; ++t)
-      for (int i = 0; i < nr; ++i) {
-        cd acc = 0;
-        for (int b = 0; b < q; ++b) acc += Ginv[(size_t)t * q + b] * std::conj(UR[(size_t)i * q + b]);
-        P[(size_t)t * nr + i] = acc;
+    for (int k = 0; k < q; ++k) {
+      if (!(su[k] > cut * su[0])) continue;
+      const double inv2 = 1.0 / (su[k] * su[k]);
+      for (int t = 0; t < q; ++t) {
+        const cd wt = Wv[(size_t)t * q + k] * inv2;
+        for (int i = 0; i < nr; ++i) P[(size_t)t * nr + i] += wt * std::conj(Y[(size_t)i * q + k]);
       }
+    }
     return P;
   };
 
   struct Sep {
     std::vector<int> C, R;
     std::vector<cd> W, P;
+    std::vector<cd> T;  // exact projection (the sample holds every column): T = S_q V_q^H
     int q = 0;
     double est = 0;
   };
   std::vector<Sep> sep(L);
   p->wedge_err.assign(L, 0.0);
-  const double svd_cut = kSvdFraction * eps;
+  const double sep_cut = opt.sep_cut > 0 ? opt.sep_cut : kSvdFraction;
+  const double sep_target = opt.sep_target > 0 ? opt.sep_target : kValidationTarget;
+  const double svd_cut = sep_cut * eps;
   for (int l = 0; l < L; ++l) {
     const WedgeDev &wd = p->wedges[l];
     const int npts = wd.npts;
@@ -797,35 +895,53 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
       }
       std::sort(C.begin(), C.end());
       const int rc = (int)C.size();
-      // SVD of A_[C] through its Gram matrix (step 2)
+      // SVD of A_[C] (step 2): A_[C] = Q R by Householder TSQR on the device,
+      // R = U_R S V^H by one-sided Jacobi; then A_[C] V = Q U_R S, so
+      // U = A_[C] V S^-1 has orthonormal columns.  The singular values keep the
+      // absolute accuracy eps_mach s_1 that a Gram matrix would square.
       fio_status s = eval_cols(l, C);
       if (s != FIO_OK) return s;
-      FIO_CK(plan_gram(d_AC, NN, rc, d_part, nparts_for(rc), d_G, 0), "Gram kernel");
-      std::vector<cd> G((size_t)rc * rc);
-      FIO_CK(cudaMemcpy(G.data(), d_G, sizeof(cd) * rc * rc, cudaMemcpyDeviceToHost), "download G");
-      std::vector<double> ev;
+      if ((s = ensure_qr(rc)) != FIO_OK) return s;
+      std::vector<cd> Rm((size_t)rc * rc);
+      FIO_CK(plan_tsqr(d_AC, NN, rc, d_qrw, d_stk0, d_stk1, reinterpret_cast<double2 *>(Rm.data()), 0),
+             "TSQR kernel");
+      FIO_CK(cudaStreamSynchronize(0), "TSQR kernel");
+      std::vector<double> sv;
       std::vector<cd> V;
-      herm_eig(rc, G, ev, V);
-      const double s1 = std::sqrt(std::max(ev[0], 0.0));
+      svd_jacobi(rc, rc, Rm, sv, V);
+      const double s1 = sv[0];
       int q = 0;
-      while (q < rc && std::sqrt(std::max(ev[q], 0.0)) > svd_cut * s1) ++q;
+      while (q < rc && sv[q] > svd_cut * s1) ++q;
       q = std::max(q, 1);
       std::vector<cd> Wm((size_t)rc * q);
       for (int i = 0; i < rc; ++i)
-        for (int t = 0; t < q; ++t) Wm[(size_t)i * q + t] = V[(size_t)i * rc + t] / std::sqrt(ev[t]);
-      // rows R and T = U_[R]^+ A_[R] (steps 3-4)
-      SplitMix64 rr{mix_seed(opt.seed, (uint64_t)l + 1, 3 * (uint64_t)attempt + 2)};
-      const int nr = (int)std::min<long long>(NN, std::max(rc, 4 * q));
-      std::vector<int> R = sample_distinct((int)NN, nr, rr);
-      std::vector<cd> UR;
-      if ((s = u_rows(R, rc, q, Wm, UR)) != FIO_OK) return s;
-      std::vector<cd> P = pinv(UR, nr, q, svd_cut);
-      FIO_CK(cudaMemcpy(d_P, P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
-      FIO_CK(cudaMemcpy(d_rx, R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
+        for (int t = 0; t < q; ++t)
+          Wm[(size_t)i * q + t] = sv[t] > 0 ? V[(size_t)i * rc + t] / sv[t] : cd(0);
+      // rows R and T = U_[R]^+ A_[R] (steps 3-4).  When the sample holds every
+      // column of the wedge, A_[C] is the whole wedge block and the projection
+      // is exact: T = U^H A = S_q V_q^H, with no row sample.
+      const bool exact = rc >= npts;
+      std::vector<int> R;
+      std::vector<cd> P, Tex;
       if ((s = regrow(&d_T, T_cap, (long long)q * npts, "alloc T")) != FIO_OK) return s;
-      FIO_CK(plan_form_beta(ph, d_xdata, N, wd, p->d_warp + (size_t)l * NN, d_rx, nr, q, d_P, d_pk1,
-                            d_pk2, nullptr, d_T, FIO_FP64, 0),
-             "T kernel");
+      if (exact) {
+        Tex.assign((size_t)q * npts, cd(0));
+        for (int t = 0; t < q; ++t)
+          for (int c = 0; c < rc; ++c) Tex[(size_t)t * npts + C[c]] = sv[t] * std::conj(V[(size_t)c * rc + t]);
+        FIO_CK(cudaMemcpy(d_T, Tex.data(), sizeof(cd) * Tex.size(), cudaMemcpyHostToDevice), "upload T");
+      } else {
+        SplitMix64 rr{mix_seed(opt.seed, (uint64_t)l + 1, 3 * (uint64_t)attempt + 2)};
+        const int nr = (int)std::min<long long>(NN, std::max(rc, 4 * q));
+        R = sample_distinct((int)NN, nr, rr);
+        std::vector<cd> UR;
+        if ((s = u_rows(R, rc, q, Wm, UR)) != FIO_OK) return s;
+        P = pinv(UR, nr, q, svd_cut);
+        FIO_CK(cudaMemcpy(d_P, P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
+        FIO_CK(cudaMemcpy(d_rx, R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
+        FIO_CK(plan_form_beta(ph, d_xdata, N, wd, p->d_warp + (size_t)l * NN, d_rx, nr, q, d_P, d_pk1,
+                              d_pk2, nullptr, d_T, FIO_FP64, 0),
+               "T kernel");
+      }
       // validation on fresh rows against every column of the wedge
       SplitMix64 rg{mix_seed(opt.seed, (uint64_t)l + 1, 3 * (uint64_t)attempt + 3)};
       std::vector<int> Gx = sample_distinct((int)NN, s_val, rg);
@@ -842,7 +958,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
       double se = 0, sn = 0;
       for (int i = 0; i < npts; ++i) { se += err[i]; sn += nrm[i]; }
       const double est = std::sqrt(se / std::max(sn, 1e-300));
-      const bool ok = (est <= kValidationTarget * eps && 3 * q <= rc) || rc >= npts;
+      const bool ok = (est <= sep_target * eps && 3 * q <= rc) || exact;
       if (ok || rc >= rank_cap) {
         if (!ok && est > eps) {
           set_error("wedge " + std::to_string(l) + ": separation error " + std::to_string(est) +
@@ -853,6 +969,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
         sep[l].R = R;
         sep[l].W = Wm;
         sep[l].P = P;
+        sep[l].T = Tex;
         sep[l].q = q;
         sep[l].est = est;
         p->wedges[l].q = q;
@@ -874,6 +991,13 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
         }
       r = std::min({2 * r, rank_cap, npts});
     }
+  }
+
+  for (double2 **q : {&d_qrw, &d_stk0, &d_stk1}) {  // the QR workspace is done
+    if (!*q) continue;
+    tmp.ptrs.erase(std::find(tmp.ptrs.begin(), tmp.ptrs.end(), (void *)*q));
+    cudaFree(*q);
+    *q = nullptr;
   }
 
   // ---- layout of the factors and grids
@@ -943,17 +1067,35 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
                            p->d_perm + (size_t)l * NN,
                            (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision, 0),
            "alpha kernel");
-    FIO_CK(cudaMemcpy(d_P, sp.P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
-    FIO_CK(cudaMemcpy(d_rx, sp.R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
     std::vector<double> dec(wd.npts);
     for (int i = 0; i < wd.npts; ++i)
       dec[i] = 1.0 / (kb_phihat_host((double)x1p[l][i] / wd.m1, w, p->kb.beta) *
                       kb_phihat_host((double)x2p[l][i] / wd.m2, w, p->kb.beta));
+    char *beta_l = (char *)p->d_beta + (size_t)wd.beta_off * cs;
+    if (!sp.T.empty()) {  // exact projection: beta' = T / phihat, formed here
+      const size_t n = (size_t)q * wd.npts;
+      if (p->precision == FIO_FP64) {
+        std::vector<cd> b(n);
+        for (size_t e = 0; e < n; ++e) b[e] = sp.T[e] * dec[e % wd.npts];
+        FIO_CK(cudaMemcpy(beta_l, b.data(), sizeof(cd) * n, cudaMemcpyHostToDevice), "upload beta");
+      } else {
+        std::vector<float> b(2 * n);
+        for (size_t e = 0; e < n; ++e) {
+          const cd v = sp.T[e] * dec[e % wd.npts];
+          b[2 * e] = (float)v.real();
+          b[2 * e + 1] = (float)v.imag();
+        }
+        FIO_CK(cudaMemcpy(beta_l, b.data(), sizeof(float) * 2 * n, cudaMemcpyHostToDevice), "upload beta");
+      }
+      continue;
+    }
+    FIO_CK(cudaMemcpy(d_P, sp.P.data(), sizeof(cd) * q * nr, cudaMemcpyHostToDevice), "upload P");
+    FIO_CK(cudaMemcpy(d_rx, sp.R.data(), sizeof(int) * nr, cudaMemcpyHostToDevice), "upload R");
     FIO_CK(cudaMemcpy(d_pk1, pk1 + wd.pt_off, sizeof(int) * wd.npts, cudaMemcpyHostToDevice), "upload points");
     FIO_CK(cudaMemcpy(d_pk2, pk2 + wd.pt_off, sizeof(int) * wd.npts, cudaMemcpyHostToDevice), "upload points");
     FIO_CK(cudaMemcpy(d_dec, dec.data(), sizeof(double) * wd.npts, cudaMemcpyHostToDevice), "upload deconvolution");
     FIO_CK(plan_form_beta(ph, d_xdata, N, wd, p->d_warp + (size_t)l * NN, d_rx, nr, q, d_P, d_pk1,
-                          d_pk2, d_dec, (char *)p->d_beta + (size_t)wd.beta_off * cs, p->precision, 0),
+                          d_pk2, d_dec, beta_l, p->precision, 0),
            "beta kernel");
   }
   FIO_CK(cudaDeviceSynchronize(), "plan construction");

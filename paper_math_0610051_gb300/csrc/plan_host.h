@@ -1,5 +1,5 @@
 // plan_host.h -- host-side helpers of the plan (wedges, boxes, KB kernel,
-// Hermitian eigensolver), shared by plan.cpp and the host utilities of api.cpp.
+// Hermitian eigensolver, Jacobi SVD), shared by plan.cpp and the host utilities of api.cpp.
 #pragma once
 
 #include <complex>
@@ -23,5 +23,7 @@ double kb_phi_host(double s, int w, double beta);
 double kb_phihat_host(double nu, int w, double beta);
 void herm_eig(int n, std::vector<std::complex<double>> A, std::vector<double> &ev,
               std::vector<std::complex<double>> &V);
+void svd_jacobi(int m, int n, std::vector<std::complex<double>> &A, std::vector<double> &sig,
+                std::vector<std::complex<double>> &V);
 
 }  // namespace fio

@@ -1,8 +1,8 @@
 // plan_kernels.cu -- FP64 device kernels of the preprocessing step (Sec. 3.2):
 // warped points y_l(x) = grad_xi Phi(x, xihat_l) (Sec. 1.4), entries of the
 // residual kernel A_{x,xi} = a(x,xi) exp(2 pi i Phi_l(x,xi)) (Eq. probform) at
-// sampled columns and rows, the Gram matrix of A_[C], and the factors
-// gamma^x = U = A_[C] V S^-1 and gamma^xi = T = U_[R]^+ A_[R].
+// sampled columns and rows, the triangular factor of A_[C] (Householder TSQR),
+// and the factors gamma^x = U = A_[C] V S^-1 and gamma^xi = T = U_[R]^+ A_[R].
 //
 // Everything here is double precision: the residual phase cancels O(N) terms
 // (Sec. 1.3), and the warped points are reduced modulo 1 to 32-bit fractions
@@ -223,67 +223,119 @@ __global__ void k_eval_cols(PhaseDev ph, const void *xd, int N, WedgeDev w,
   AC[idx] = entry(ph, xview(ph, xd), N, w, x, warp_l[x], ck1[c], ck2[c]);
 }
 
-// Gram of A (rows x r): upper tiles of 32 x 32 over row chunks (partials),
-// then an ordered sum over chunks (deterministic).
-constexpr int kGT = 32, kGR = 32;
+// Householder QR of the row panels of a tall matrix `in` (rows x r, row-major),
+// the first step of the tall-skinny QR (TSQR) of A_[C].  CTA p copies rows
+// [p P, p P + h) into its own region of `work` and reduces them to upper
+// triangular form with h' = min(h, r) reflectors H_k = I - u u^H (u^H u = 2, u
+// zero above row k; u is kept in column k, R_kk in rdiag).  It writes its r x r
+// factor R_p (zero below the diagonal and in rows >= h') to Rout[p].  Stacking
+// the R_p and factoring the stack again gives the R of the whole matrix; the Q
+// factors are never formed.
+//
+// Threads: lane -> column j (stride 32), warp -> row group i = k + warp (stride
+// 8), so the reads of a row are coalesced and u_i is a broadcast.
+constexpr int kQrThreads = 256;
+constexpr int kQrGroups = kQrThreads / 32;
 
-__global__ void __launch_bounds__(256) k_gram_partial(const double2 *__restrict__ A,
-                                                      long long rows, int r, int ntile,
-                                                      double2 *__restrict__ partial,
-                                                      int nparts) {
-  __shared__ double2 Ai[kGR][kGT], Aj[kGR][kGT];
-  int tile = blockIdx.x, bi = 0;
-  while (tile >= ntile - bi) {
-    tile -= ntile - bi;
-    ++bi;
-  }
-  const int bj = bi + tile;
-  const int part = blockIdx.y;
-  const long long chunk = (rows + nparts - 1) / nparts;
-  const long long r0 = part * chunk, r1 = min(rows, r0 + chunk);
-  const int ti = threadIdx.x / 8, tj = (threadIdx.x % 8) * 4;
-  double2 acc[4];
-  for (int k = 0; k < 4; ++k) acc[k] = make_double2(0.0, 0.0);
-  for (long long rb = r0; rb < r1; rb += kGR) {
-    for (int e = threadIdx.x; e < kGR * kGT; e += blockDim.x) {
-      const int rr = e / kGT, cc = e % kGT;
-      const long long row = rb + rr;
-      const int ci = bi * kGT + cc, cj = bj * kGT + cc;
-      Ai[rr][cc] = (row < r1 && ci < r) ? A[row * r + ci] : make_double2(0.0, 0.0);
-      Aj[rr][cc] = (row < r1 && cj < r) ? A[row * r + cj] : make_double2(0.0, 0.0);
+__device__ __forceinline__ double warp_sum_d(double v) {
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+  return v;
+}
+
+__global__ void __launch_bounds__(kQrThreads)
+k_panel_qr(const double2 *__restrict__ in, long long rows, int r, int P, double2 *__restrict__ work,
+           double2 *__restrict__ Rout) {
+  extern __shared__ double2 qsm[];
+  double2 *dots = qsm;                // [kQrGroups][r] partial u^H a_j, then the sums in row 0
+  double2 *rdiag = dots + kQrGroups * r;
+  __shared__ double red[kQrGroups];
+  __shared__ double s_scale;
+  const long long row0 = (long long)blockIdx.x * P;
+  const int h = (int)min((long long)P, rows - row0);
+  double2 *a = work + row0 * r;
+  const double2 *src = in + row0 * r;
+  const long long ne = (long long)h * r;
+  for (long long e = threadIdx.x; e < ne; e += kQrThreads) a[e] = src[e];
+  __syncthreads();
+  const int lane = threadIdx.x & 31, rg = threadIdx.x >> 5;
+  const int kmax = min(h, r);
+  for (int k = 0; k < kmax; ++k) {
+    double s2 = 0.0;
+    for (int i = k + threadIdx.x; i < h; i += kQrThreads) {
+      const double2 v = a[(long long)i * r + k];
+      s2 += v.x * v.x + v.y * v.y;
+    }
+    s2 = warp_sum_d(s2);
+    if (lane == 0) red[rg] = s2;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double sig2 = 0.0;
+      for (int w = 0; w < kQrGroups; ++w) sig2 += red[w];
+      const double sigma = sqrt(sig2);
+      const double2 x0 = a[(long long)k * r + k];
+      const double ax0 = hypot(x0.x, x0.y);
+      if (sigma == 0.0) {
+        rdiag[k] = make_double2(0.0, 0.0);
+        s_scale = 0.0;
+      } else {
+        // alpha = -phase(x0) sigma: no cancellation in x0 - alpha
+        const double2 ph = ax0 > 0.0 ? make_double2(x0.x / ax0, x0.y / ax0) : make_double2(1.0, 0.0);
+        const double2 alpha = make_double2(-ph.x * sigma, -ph.y * sigma);
+        const double sc = 1.0 / sqrt(sigma * (sigma + ax0));  // u = (x - alpha e1) sc, u^H u = 2
+        rdiag[k] = alpha;
+        a[(long long)k * r + k] = make_double2((x0.x - alpha.x) * sc, (x0.y - alpha.y) * sc);
+        s_scale = sc;
+      }
     }
     __syncthreads();
-    for (int rr = 0; rr < kGR; ++rr) {
-      const double2 a = Ai[rr][ti];
-      for (int k = 0; k < 4; ++k) {
-        const double2 b = Aj[rr][tj + k];
-        acc[k].x += a.x * b.x + a.y * b.y;  // conj(a) b
-        acc[k].y += a.x * b.y - a.y * b.x;
+    const double sc = s_scale;
+    if (sc == 0.0) continue;  // a zero column: H_k = I (uniform across the CTA)
+    for (int i = k + 1 + threadIdx.x; i < h; i += kQrThreads) {
+      double2 &v = a[(long long)i * r + k];
+      v = make_double2(v.x * sc, v.y * sc);
+    }
+    __syncthreads();
+    // w_j = u^H a_j for the trailing columns
+    for (int j = k + 1 + lane; j < r; j += 32) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int i = k + rg; i < h; i += kQrGroups) {
+        const double2 u = a[(long long)i * r + k], v = a[(long long)i * r + j];
+        acc.x += u.x * v.x + u.y * v.y;
+        acc.y += u.x * v.y - u.y * v.x;
+      }
+      dots[rg * r + j] = acc;
+    }
+    __syncthreads();
+    for (int j = k + 1 + threadIdx.x; j < r; j += kQrThreads) {
+      double2 sum = dots[j];
+      for (int g = 1; g < kQrGroups; ++g) {
+        const double2 v = dots[g * r + j];
+        sum.x += v.x;
+        sum.y += v.y;
+      }
+      dots[j] = sum;
+    }
+    __syncthreads();
+    // a_j -= u w_j
+    for (int j = k + 1 + lane; j < r; j += 32) {
+      const double2 wj = dots[j];
+      for (int i = k + rg; i < h; i += kQrGroups) {
+        const double2 u = a[(long long)i * r + k];
+        double2 &v = a[(long long)i * r + j];
+        v.x -= u.x * wj.x - u.y * wj.y;
+        v.y -= u.x * wj.y + u.y * wj.x;
       }
     }
     __syncthreads();
   }
-  const int i = bi * kGT + ti;
-  for (int k = 0; k < 4; ++k) {
-    const int j = bj * kGT + tj + k;
-    if (i < r && j < r) partial[(long long)part * r * r + (long long)i * r + j] = acc[k];
+  double2 *R = Rout + (long long)blockIdx.x * r * r;
+  for (int e = threadIdx.x; e < r * r; e += kQrThreads) {
+    const int i = e / r, j = e - (e / r) * r;
+    double2 v = make_double2(0.0, 0.0);
+    if (i < kmax && j >= i) v = j == i ? rdiag[i] : a[(long long)i * r + j];
+    R[e] = v;
   }
-}
-
-__global__ void k_gram_reduce(const double2 *__restrict__ partial, int nparts, int r,
-                              double2 *__restrict__ G) {
-  const int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  if (idx >= r * r) return;
-  const int i = idx / r, j = idx % r;
-  if (j < i || (j / kGT) < (i / kGT)) return;
-  double2 s = make_double2(0.0, 0.0);
-  for (int p = 0; p < nparts; ++p) {
-    const double2 v = partial[(long long)p * r * r + idx];
-    s.x += v.x;
-    s.y += v.y;
-  }
-  G[i * r + j] = s;
-  G[j * r + i] = make_double2(s.x, -s.y);
 }
 
 template <typename C>
@@ -430,13 +482,34 @@ cudaError_t plan_eval_cols(const PhaseDev &ph, const void *d_xdata, int N, const
   return cudaGetLastError();
 }
 
-cudaError_t plan_gram(const double2 *d_AC, long long rows, int r, double2 *d_partial, int nparts,
-                      double2 *d_G, cudaStream_t s) {
-  const int ntile = (r + kGT - 1) / kGT;
-  const int ntiles = ntile * (ntile + 1) / 2;
-  k_gram_partial<<<dim3(ntiles, nparts), 256, 0, s>>>(d_AC, rows, r, ntile, d_partial, nparts);
-  k_gram_reduce<<<blocks((long long)r * r, 256), 256, 0, s>>>(d_partial, nparts, r, d_G);
-  return cudaGetLastError();
+int tsqr_panel_rows(int r) { return r * 4 > 128 ? r * 4 : 128; }
+
+size_t tsqr_stack_elems(long long rows, int r) {
+  const long long P = tsqr_panel_rows(r);
+  return (size_t)((rows + P - 1) / P) * r * r;
+}
+
+cudaError_t plan_tsqr(const double2 *d_A, long long rows, int r, double2 *d_work, double2 *d_stk0,
+                      double2 *d_stk1, double2 *h_R, cudaStream_t s) {
+  const int P = tsqr_panel_rows(r);
+  const size_t smem = (size_t)(kQrGroups + 1) * r * sizeof(double2);
+  cudaError_t e = cudaFuncSetAttribute(k_panel_qr, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  double2 *stk[2] = {d_stk0, d_stk1};
+  const double2 *in = d_A;
+  long long n = rows;
+  int lvl = 0;
+  for (;;) {
+    const long long np = (n + P - 1) / P;
+    k_panel_qr<<<(unsigned)np, kQrThreads, smem, s>>>(in, n, r, P, d_work, stk[lvl & 1]);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    if (np == 1) break;
+    in = stk[lvl & 1];
+    n = np * r;
+    ++lvl;
+  }
+  return cudaMemcpyAsync(h_R, stk[lvl & 1], sizeof(double2) * r * r, cudaMemcpyDeviceToHost, s);
 }
 
 cudaError_t plan_form_alpha(const double2 *d_AC, int N, int r, int q, const double2 *d_W,

@@ -40,7 +40,8 @@ class _Options(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("L", ctypes.c_int), ("sigma", ctypes.c_double),
                 ("kb_width", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("r0", ctypes.c_int),
                 ("rank_cap", ctypes.c_int), ("max_batch", ctypes.c_int),
-                ("surrogate", ctypes.c_void_p), ("surrogate_warp_budget", ctypes.c_double)]
+                ("surrogate", ctypes.c_void_p), ("surrogate_warp_budget", ctypes.c_double),
+                ("sep_cut", ctypes.c_double), ("sep_target", ctypes.c_double)]
 
 
 class _SurInfo(ctypes.Structure):
@@ -83,7 +84,7 @@ EXPORTS = [
     "fio_plan_get_info", "fio_plan_get_wedge", "fio_plan_export_wedge", "fio_plan_export_warp",
     "fio_plan_destroy", "fio_plan_set_timing", "fio_plan_stage_times",
     "fio_dft2", "fio_default_wedges", "fio_wedge_map", "fio_wedge_geometry", "fio_kb_eval",
-    "fio_kb_width_for", "fio_host_eigh", "fio_status_string", "fio_last_error", "fio_version",
+    "fio_kb_width_for", "fio_host_eigh", "fio_host_svd", "fio_status_string", "fio_last_error", "fio_version",
     "fio_surrogate_train", "fio_surrogate_destroy", "fio_surrogate_get_info", "fio_surrogate_params",
     "fio_surrogate_eval", "fio_surrogate_loss_grad", "fio_surrogate_samples", "fio_surrogate_nparams",
 ]
@@ -124,6 +125,7 @@ def lib():
             L.fio_kb_eval.argtypes = [I, D, I, P, P, P, P]
             L.fio_kb_width_for.argtypes = [D]
             L.fio_host_eigh.argtypes = [I, P, P, P]
+            L.fio_host_svd.argtypes = [I, I, P, P, P, P]
             L.fio_surrogate_train.argtypes = [ctypes.POINTER(_Phase), I, I, I, ctypes.c_ulonglong,
                                               ctypes.POINTER(P)]
             L.fio_surrogate_destroy.argtypes = [P]
@@ -172,7 +174,8 @@ class Plan:
     def __init__(self, N: int, phase: int, params, eps: float, amp=None, precision: str = "mixed",
                  L: int = 0, sigma: float = 0.0, kb_width: int = 0, seed: int = 0x5EED5EED,
                  r0: int = 0, rank_cap: int = 0, max_batch: int = 1, device=None,
-                 surrogate: "Surrogate | None" = None, surrogate_warp_budget: float = 0.0):
+                 surrogate: "Surrogate | None" = None, surrogate_warp_budget: float = 0.0,
+                 sep_cut: float = 0.0, sep_target: float = 0.0):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -194,6 +197,7 @@ class Plan:
         opt.seed, opt.r0, opt.rank_cap, opt.max_batch = int(seed), int(r0), int(rank_cap), int(max_batch)
         opt.surrogate = surrogate._handle if surrogate is not None else None
         opt.surrogate_warp_budget = float(surrogate_warp_budget)
+        opt.sep_cut, opt.sep_target = float(sep_cut), float(sep_target)
         self._surrogate = surrogate
         self.N = int(N)
         self.precision = opt.precision
@@ -443,3 +447,14 @@ def host_eigh(A: np.ndarray):
     V = np.empty((n, n), np.complex128)
     _check(lib().fio_host_eigh(n, _np_ptr(A), _np_ptr(ev), _np_ptr(V)), "fio_host_eigh")
     return ev, V
+
+
+def host_svd(A: np.ndarray):
+    """(s, AV, V) of fio_host_svd: A V = AV, s descending, AV's columns s_j u_j."""
+    A = np.ascontiguousarray(A, np.complex128)
+    m, n = A.shape
+    s = np.empty(n)
+    AV = np.empty((m, n), np.complex128)
+    V = np.empty((n, n), np.complex128)
+    _check(lib().fio_host_svd(m, n, _np_ptr(A), _np_ptr(s), _np_ptr(AV), _np_ptr(V)), "fio_host_svd")
+    return s, AV, V

@@ -242,3 +242,62 @@ def test_hankel_amplitude_sign_is_validated(fio):
 def fio_synth():
     from paper_math_0610051_gb300 import synth
     return synth
+
+
+def _unitary(g, n):
+    q, r = np.linalg.qr(g.standard_normal((n, n)) + 1j * g.standard_normal((n, n)))
+    return q * (np.diag(r) / np.abs(np.diag(r)))
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (5, 3), (40, 40), (200, 24), (7, 12)])
+def test_host_svd_matches_numpy(fio, m, n):
+    """One-sided Jacobi SVD (the solver of the randomized separation, Sec. 3.2)
+    against LAPACK's: singular values, A V = AV, orthonormal V, orthogonal
+    columns of AV with norms s."""
+    g = np.random.default_rng(m * 131 + n)
+    A = g.standard_normal((m, n)) + 1j * g.standard_normal((m, n))
+    s, AV, V = fio.host_svd(A)
+    ref = np.linalg.svd(A, compute_uv=False)
+    k = min(m, n)
+    assert np.all(np.diff(s) <= 0)
+    assert np.max(np.abs(s[:k] - ref[:k])) < 1e-13 * ref[0]
+    assert np.all(np.abs(s[k:]) < 1e-13 * ref[0])
+    assert np.max(np.abs(A @ V - AV)) < 1e-13 * ref[0]
+    assert np.max(np.abs(V.conj().T @ V - np.eye(n))) < 1e-13
+    G = AV.conj().T @ AV
+    assert np.max(np.abs(G - np.diag(s ** 2))) < 1e-13 * ref[0] ** 2
+
+
+def test_host_svd_small_singular_values_keep_absolute_accuracy(fio):
+    """A = U diag(s) V^H with s from 1 down to 1e-12: every computed singular value
+    is within a few 1e-16 s_1 of the true one, as for a QR-based SVD.  The square
+    roots of the eigenvalues of A^H A (the Gram route) miss the small ones: their
+    error grows like 1e-16 s_1^2 / s_k."""
+    g = np.random.default_rng(7)
+    n, m = 16, 64
+    sv = np.logspace(0, -12, n)
+    U = _unitary(g, m)[:, :n]
+    Vt = _unitary(g, n)
+    A = (U * sv) @ Vt.conj().T
+    s, AV, V = fio.host_svd(A)
+    assert np.max(np.abs(s - sv)) < 2e-15
+    # the Gram route, for contrast
+    ev = np.linalg.eigvalsh(A.conj().T @ A)[::-1]
+    gram = np.sqrt(np.maximum(ev, 0))
+    assert np.max(np.abs(gram - sv)) > 1e-10
+    # right singular vectors of well-separated singular values are accurate
+    for k in range(4):
+        assert abs(abs(np.vdot(V[:, k], Vt[:, k])) - 1) < 1e-12
+
+
+def test_host_svd_rank_deficient_and_zero(fio):
+    g = np.random.default_rng(3)
+    B = g.standard_normal((30, 4)) + 1j * g.standard_normal((30, 4))
+    A = B @ (g.standard_normal((4, 9)) + 1j * g.standard_normal((4, 9)))
+    s, AV, V = fio.host_svd(A)
+    ref = np.linalg.svd(A, compute_uv=False)
+    assert np.max(np.abs(s[:4] - ref[:4])) < 1e-13 * ref[0]
+    assert np.max(s[4:]) < 1e-13 * ref[0]
+    s0, AV0, V0 = fio.host_svd(np.zeros((6, 3)))
+    assert np.all(s0 == 0) and np.all(AV0 == 0)
+    assert np.allclose(V0.conj().T @ V0, np.eye(3))
