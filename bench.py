@@ -30,11 +30,11 @@ sys.path.insert(0, ROOT)
 METRIC = "FIO outputs/s at N=1024, rel-L2<=1e-4 (mixed vs FP64 path), % HBM roofline"
 UNIT = "outputs/s"
 FALLBACK_HBM_GBS = 6800.0
-# FP32 peak: 152 SMs x 128 FP32 lanes x 2 flop per FMA x 2.07 GHz (maximum SM clock)
-FP32_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+FP32_LANES_PER_SM = 128  # Blackwell SM: 4 partitions x 32 FP32 lanes, one FMA (2 flop) per lane and clock
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "traffic.json")
 KERNEL_SRCS = [os.path.join(ROOT, "paper_math_0610051_gb300", "csrc", f)
-               for f in ("interp.cu", "apply.cu", "apply_common.cuh", "fft_engine.cuh")]
+               for f in ("interp_tasks.cu", "spread.cu", "bin_common.cuh", "apply.cu",
+                         "apply_common.cuh", "fft_engine.cuh")]
 
 
 def log(*a):
@@ -176,6 +176,25 @@ class ClockSampler:
                 "reasons": sorted(reasons)}
 
 
+def fp32_peak(dev, clocks):
+    """FP32 peak in TFLOP/s from the device's SM count and the median SM clock
+    sampled during the timed region (the maximum clock if no sample was taken)."""
+    import torch
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    mhz, src = None, "median sampled SM clock"
+    if clocks:
+        mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz")
+    if not mhz:
+        try:
+            out = subprocess.run(["nvidia-smi", "--query-gpu=clocks.max.sm", "--format=csv,noheader,nounits",
+                                  "-i", str(dev.index or 0)], capture_output=True, text=True, timeout=10)
+            mhz, src = float(out.stdout.strip().splitlines()[0]), "maximum SM clock"
+        except Exception:
+            mhz, src = 2070.0, "recipe's maximum SM clock (no nvidia-smi)"
+    tf = sms * FP32_LANES_PER_SM * 2 * mhz * 1e6 / 1e12
+    return tf, f"derived: {sms} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x {mhz:.0f} MHz ({src})"
+
+
 def stage_bytes(plan, B):
     """Algorithmic HBM bytes of each stage for one launch on B inputs (complex64)."""
     info = plan.info()
@@ -232,6 +251,20 @@ def cpu_oracle_rate(N, f0, budget_s=15.0, out0=None):
     t_pts = time.perf_counter() - t0
     err = orc.rel_l2(ref, out0[n1, n2]) if out0 is not None else None
     return s / (t_dft + t_pts), orc.num_threads(), s, err
+
+
+def cpu_oracle_adjoint_err(N, g0, adj0, npts=64):
+    """rel-L2 of the adjoint's spectrum at npts random frequencies against the
+    oracle's direct sums of Sec. 3.5 (FP64)."""
+    import numpy as np
+    from oracle import oracle as orc
+    from paper_math_0610051_gb300 import synth
+    ph = orc.Phase(orc.ELLIPSE, synth.ellipse_params())
+    gen = np.random.default_rng(17)
+    k1, k2 = gen.integers(-N // 2, N // 2, npts), gen.integers(-N // 2, N // 2, npts)
+    ref = orc.adjoint_hat_points(ph, orc.Amplitude(), g0, k1, k2)
+    spec = orc.dft2(np.asarray(adj0, np.complex128))
+    return orc.rel_l2(ref, spec[k1 + N // 2, k2 + N // 2])
 
 
 def run_reference(a, world, rank):
@@ -339,15 +372,16 @@ def run_ours(a, world, rank, local):
     per_launch_s = top_ms / max(top_cnt, 1) / 1e3
     achieved = sb[top] / per_launch_s / 1e9
     peak, peak_kind = peaks()
-    kname = {"S3_interp": "k_interp_bin", "S4a_spread": "k_spread_bin"}.get(top, top)
+    kname = {"S3_interp": "k_interp_tasks", "S4a_spread": "k_spread_sweep"}.get(top, top)
     traffic = recorded_traffic(kname, B, N)
     sf = stage_flops(plan, B)
-    if top in sf and sf[top] / sb[top] > FP32_PEAK_TFLOPS * 1e12 / (peak * 1e9):
+    fp32_tf, fp32_src = fp32_peak(dev, clocks)
+    if top in sf and sf[top] / sb[top] > fp32_tf * 1e12 / (peak * 1e9):
         # arithmetic intensity above the ridge point: the FP32 pipe bounds the kernel
         tf = sf[top] / per_launch_s / 1e12
-        roofline = {"bound": "alu", "achieved": tf, "peak": FP32_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": tf / FP32_PEAK_TFLOPS, "traffic": traffic, "kernel": top,
-                    "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2 x 2.07 GHz",
+        roofline = {"bound": "alu", "achieved": tf, "peak": fp32_tf, "unit": "TFLOP/s",
+                    "frac": tf / fp32_tf, "traffic": traffic, "kernel": top,
+                    "peak_source": fp32_src,
                     "flops_per_launch": sf[top], "alg_bytes_per_launch": sb[top],
                     "hbm_achieved_gbs": achieved, "hbm_peak_gbs": peak,
                     "hbm_frac": achieved / peak, "hbm_peak_source": peak_kind,
@@ -402,6 +436,9 @@ def run_ours(a, world, rank, local):
         o64 = p64.apply(f64)
         rel = float(torch.linalg.vector_norm(o64 - lf[:1].to(torch.complex128)) /
                     torch.linalg.vector_norm(o64))
+        a64 = p64.adjoint(g64)
+        rel_adj = float(torch.linalg.vector_norm(a64 - lsg[:1].to(torch.complex128)) /
+                        torch.linalg.vector_norm(a64))
         for _ in range(2):
             p64.apply(f64)
             p64.adjoint(g64)
@@ -415,6 +452,7 @@ def run_ours(a, world, rank, local):
         torch.cuda.synchronize()
         ms64 = e0.elapsed_time(e1)
         extra["rel_l2_mixed_vs_fp64"] = rel
+        extra["rel_l2_mixed_vs_fp64_adjoint"] = rel_adj
         extra["fp64_path"] = {"outputs_per_s": 2 * N * N * k64 / (ms64 / 1e3), "batch": 1,
                               "ms_per_step": ms64 / k64}
         p64.close()
@@ -425,6 +463,7 @@ def run_ours(a, world, rank, local):
             "sample": f"forward direct sums (Eq. dfio, FP64) at {s} random x of input 0, "
                       f"its {N}x{N} DFT included"}
         extra["rel_l2_vs_oracle"] = err
+        extra["rel_l2_vs_oracle_adjoint"] = cpu_oracle_adjoint_err(N, g_np[0], lsg[0].cpu().numpy())
     if rank != 0:
         return
     line = {

@@ -140,7 +140,9 @@ fio_status fio_plan_create(int N, const fio_phase *phase, const fio_amplitude *a
  * One plan must not be used on two streams at the same time (shared workspace).
  * The sum over wedges is accumulated with atomic adds into out, so the last bit
  * of a result may differ between runs (the order of the additions is not
- * fixed); every other step, and the whole adjoint, is deterministic. */
+ * fixed); every other step, and the whole adjoint, is deterministic: the same
+ * call gives the same bits.  The order of the adjoint's spread sums depends on
+ * the batch size, so one input may differ in its last bits between batch sizes. */
 fio_status fio_apply(fio_plan plan, const void *f, void *out, int batch, void *stream);
 
 /* out = L* g (Sec. 3.5: gamma^x-conjugate multiply, type-1 NUFFT, conj(gamma^xi)
@@ -380,6 +382,14 @@ fio_status fio_host_eigh(int n, const double *A, double *evals, double *V);
  * singular values keep an absolute accuracy of about 1e-16 s_1.  Any output
  * pointer may be NULL. */
 fio_status fio_host_svd(int m, int n, const double *A, double *s, double *AV, double *V);
+
+/* Singular values s (descending) and right singular vectors V (columns, n x n
+ * row-major interleaved) of a square n x n complex matrix R (host; n <= 2048) by
+ * one-sided Jacobi preconditioned with a column-pivoted QR: R P = Q1 R1, then
+ * Jacobi on R1^H, which converges in a few sweeps.  This is the solver the
+ * randomized separation (Sec. 3.2) applies to the triangular factor of A_[C].
+ * A column of V whose singular value is 0 is returned as zeros. */
+fio_status fio_host_svd_right(int n, const double *R, double *s, double *V);
 
 const char *fio_status_string(fio_status s);
 const char *fio_last_error(void);

@@ -458,4 +458,23 @@ fio_status fio_host_svd(int m, int n, const double *A, double *s, double *AV, do
   return FIO_OK;
 }
 
+fio_status fio_host_svd_right(int n, const double *R, double *s, double *V) {
+  if (n < 1 || n > 2048 || !R || !s || !V) {
+    set_error("fio_host_svd_right: bad arguments");
+    return FIO_EINVAL;
+  }
+  using cd = std::complex<double>;
+  std::vector<cd> M((size_t)n * n);
+  for (size_t i = 0; i < M.size(); ++i) M[i] = cd(R[2 * i], R[2 * i + 1]);
+  std::vector<double> sig;
+  std::vector<cd> Vm;
+  svd_right_pivoted(n, M, sig, Vm);
+  for (int i = 0; i < n; ++i) s[i] = sig[i];
+  for (size_t i = 0; i < Vm.size(); ++i) {
+    V[2 * i] = Vm[i].real();
+    V[2 * i + 1] = Vm[i].imag();
+  }
+  return FIO_OK;
+}
+
 }  // extern "C"

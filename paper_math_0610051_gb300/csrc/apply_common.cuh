@@ -39,6 +39,14 @@ __device__ __forceinline__ void cp_async(void *smem, const void *gmem) {
 __device__ __forceinline__ void cp_async_wait() {
   asm volatile("cp.async.wait_all;\n" ::: "memory");
 }
+// Close the group of this thread's copies issued since the last commit; then
+// cp_async_wait_group<n>() waits until at most n of its groups are pending.
+__device__ __forceinline__ void cp_async_commit() {
+  asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N> __device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
 // One complex element (8 or 16 bytes).
 template <typename C>
 __device__ __forceinline__ void cp_async_elem(C *smem, const C *gmem) {

@@ -118,8 +118,9 @@ struct fio_plan_s {
   uint32_t *d_perm = nullptr;     // sorted position -> x = n1 N + n2, [l][pos]
   int *d_cstart = nullptr;        // per wedge: first sorted position of every bucket key (+ end)
   int4 *d_items = nullptr;        // interpolation work: (l, bin, first pos, end pos)
-  int2 *d_bins = nullptr;         // spread work: (l, bin), every bin of every wedge
-  int n_items = 0, n_bins = 0;
+  int2 *d_bins = nullptr;         // FP64 spread work: (l, first bin of a pair of adjacent bins)
+  int2 *d_bins1 = nullptr;        // mixed-precision spread work: (l, bin), every bin of every wedge
+  int n_items = 0, n_bins = 0, n_bins1 = 0;
   fio::HornerDev horner{};
   void *d_grid = nullptr;         // NUFFT grids [l][g1][g2][b*q + t]
   void *d_fhat = nullptr;         // spectrum workspace, batch * N * N complex
@@ -166,7 +167,10 @@ cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int bat
                         const FftPlanDev *d_plan, const void *d_tw, cudaStream_t s);
 size_t apply_smem_bytes(int n, int nl, int precision);
 // interp.cu
-constexpr int kItemPts = 1024;  // most points of one interpolation work item
+constexpr int kItemPts = 1024;  // most points of one interpolation work item (w <= 6)
+// Most points of one work item for KB width w: the mixed-precision S3 keeps the
+// weights of a whole item in shared memory, so wider windows take smaller items.
+inline int item_points(int w) { return w <= 6 ? kItemPts : kItemPts / 2; }
 // Sort wedge l's points by window-start cell: fills d_perm[l], d_warps[l], the
 // bucket table at d_cstart + key_off (synchronises; host counting sort, stable in x).
 cudaError_t sort_wedge_points(fio_plan_s *p, int l, std::vector<int> &cstart_host);
@@ -175,6 +179,12 @@ cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> 
 void fit_horner(fio_plan_s *p);           // host: piecewise-polynomial KB weights
 cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B, cudaStream_t s);
 cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s);
+// interp_tasks.cu: the mixed-precision S3 (zeroes out, then accumulates).
+cudaError_t launch_interp_tasks(const fio_plan_s *p, const void *grid, void *out, int B,
+                                cudaStream_t s);
+// spread.cu: the mixed-precision S4a, all inputs of a launch in one sweep.
+cudaError_t launch_spread_sweep(const fio_plan_s *p, const void *g, void *grid, int B,
+                                cudaStream_t s);
 void release_timing_events(fio_plan_s *p);
 
 // plan_kernels.cu (FP64 plan construction on the device)

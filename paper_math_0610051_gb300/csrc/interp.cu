@@ -31,6 +31,7 @@
 #include <vector>
 
 #include "apply_common.cuh"
+#include "bin_common.cuh"
 #include "fio_internal.h"
 
 namespace fio {
@@ -72,36 +73,6 @@ __global__ void k_gather_warp(const uint2 *__restrict__ warp_l, const uint32_t *
 }
 
 // ------------------------------------------------------------- helpers -----
-
-// KB weights of one axis: Horner polynomials (FP32) or the Bessel form (FP64).
-template <typename T, int W>
-__device__ __forceinline__ void kb_weights(T base, const KbDev &kb, const HornerDev &hz, T *wgt) {
-  if constexpr (sizeof(T) == 4) {
-    const float t = 2.0f * (base - (0.5f * W - 1.0f)) - 1.0f;
-#pragma unroll
-    for (int a = 0; a < W; ++a) wgt[a] = hz.c[hz.deg][a];
-    for (int k = hz.deg - 1; k >= 0; --k) {
-#pragma unroll
-      for (int a = 0; a < W; ++a) wgt[a] = fmaf(wgt[a], t, hz.c[k][a]);
-    }
-  } else {
-    const T tw = T(2) / T(W), beta = T(kb.beta), inv = T(kb.inv_i0b);
-#pragma unroll
-    for (int a = 0; a < W; ++a) wgt[a] = kb_phi(base - T(a), tw, beta, inv);
-  }
-}
-
-// Window start cell (s1, s2) of a warped point and its 2W weights.
-template <typename T, int W>
-__device__ __forceinline__ int2 point_weights(uint2 Y, int m1, int m2, const KbDev &kb,
-                                              const HornerDev &hz, T *wt) {
-  T b1, b2;
-  const int j01 = kb_first<T>(Y.x, m1, W, &b1);
-  const int j02 = kb_first<T>(Y.y, m2, W, &b2);
-  kb_weights<T, W>(b1, kb, hz, wt);
-  kb_weights<T, W>(b2, kb, hz, wt + W);
-  return make_int2(imodp(j01, m1), imodp(j02, m2));
-}
 
 // Start copying `nu` units (starting at complex channel cbase) of every footprint
 // cell into sG, cell-major: sG[cell * nu + k] (asynchronous: cp_async_wait and a
@@ -149,37 +120,6 @@ __device__ __forceinline__ void add_out(double2 *o, double re, double im) {
   atomicAdd(&o->x, re);
   atomicAdd(&o->y, im);
 }
-
-// A 16-byte unit of rank terms: two complex64 terms or one complex128 term.
-template <typename T> struct UnitT;
-template <> struct UnitT<float> { using type = float4; };
-template <> struct UnitT<double> { using type = double2; };
-__device__ __forceinline__ void ufma(float4 &a, float w, const float4 &v) {
-  const float2 ww = make_float2(w, w);
-  const float2 lo = ffma2(ww, make_float2(v.x, v.y), make_float2(a.x, a.y));
-  const float2 hi = ffma2(ww, make_float2(v.z, v.w), make_float2(a.z, a.w));
-  a = make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-__device__ __forceinline__ void uscale(float4 &v, float w) {
-  const float2 ww = make_float2(w, w);
-  const float2 lo = fmul2(ww, make_float2(v.x, v.y));
-  const float2 hi = fmul2(ww, make_float2(v.z, v.w));
-  v = make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-__device__ __forceinline__ void uscale(double2 &v, double w) {
-  v.x *= w;
-  v.y *= w;
-}
-__device__ __forceinline__ void ufma(double2 &a, double w, const double2 &v) {
-  a.x = fma(w, v.x, a.x);
-  a.y = fma(w, v.y, a.y);
-}
-template <typename U, typename T> __device__ __forceinline__ void ufma4(U &a, T w, const U &v) {
-  ufma(a, w, v);
-}
-template <typename U> __device__ __forceinline__ U uzero();
-template <> __device__ __forceinline__ float4 uzero<float4>() { return make_float4(0.f, 0.f, 0.f, 0.f); }
-template <> __device__ __forceinline__ double2 uzero<double2>() { return make_double2(0.0, 0.0); }
 
 // -------------------------------------------------------------------- S3 ---
 
@@ -594,7 +534,7 @@ cudaError_t sort_wedge_points(fio_plan_s *p, int l, std::vector<int> &cs) {
 
 cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> &cstart) {
   std::vector<int4> items;
-  std::vector<int2> bins;
+  std::vector<int2> bins, bins1;
   const int W = p->kb.w;
   long long nonempty = 0, total = 0;
   int maxb = 0;
@@ -604,8 +544,10 @@ cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> 
     const std::vector<int> &cs = cstart[l];
     for (int bin = 0; bin < w.nb1 * w.nb2; ++bin) {
       const int beg = cs[(size_t)bin * kBin * kBin], end = cs[(size_t)(bin + 1) * kBin * kBin];
-      for (int c = beg; c < end; c += kItemPts) items.push_back(make_int4(l, bin, c, std::min(end, c + kItemPts)));
+      const int ipts = item_points(W);
+      for (int c = beg; c < end; c += ipts) items.push_back(make_int4(l, bin, c, std::min(end, c + ipts)));
       if ((bin % w.nb2) % 2 == 0) bins.push_back(make_int2(l, bin));  // first bin of a pair
+      bins1.push_back(make_int2(l, bin));
       if (end > beg) {
         ++nonempty;
         total += end - beg;
@@ -627,12 +569,17 @@ cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> 
   }
   p->n_items = (int)items.size();
   p->n_bins = (int)bins.size();
+  p->n_bins1 = (int)bins1.size();
   p->max_bin_pts = maxb;
   p->mean_bin_pts = nonempty ? (double)total / nonempty : 0.0;
   p->max_cand = (int)maxc;
   cudaError_t e = cudaMalloc(&p->d_items, sizeof(int4) * std::max<size_t>(1, items.size()));
   if (e != cudaSuccess) return e;
   e = cudaMalloc(&p->d_bins, sizeof(int2) * std::max<size_t>(1, bins.size()));
+  if (e != cudaSuccess) return e;
+  e = cudaMalloc(&p->d_bins1, sizeof(int2) * std::max<size_t>(1, bins1.size()));
+  if (e != cudaSuccess) return e;
+  e = cudaMemcpy(p->d_bins1, bins1.data(), sizeof(int2) * bins1.size(), cudaMemcpyHostToDevice);
   if (e != cudaSuccess) return e;
   if (!items.empty())
     e = cudaMemcpy(p->d_items, items.data(), sizeof(int4) * items.size(), cudaMemcpyHostToDevice);
@@ -643,12 +590,12 @@ cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> 
 cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B,
                           cudaStream_t s) {
   if (p->precision == FIO_FP64) return dispatch_w<double>(p, nullptr, (void *)grid, out, B, false, s);
-  return dispatch_w<float>(p, nullptr, (void *)grid, out, B, false, s);
+  return launch_interp_tasks(p, grid, out, B, s);
 }
 
 cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s) {
   if (p->precision == FIO_FP64) return dispatch_w<double>(p, g, grid, nullptr, B, true, s);
-  return dispatch_w<float>(p, g, grid, nullptr, B, true, s);
+  return launch_spread_sweep(p, g, grid, B, s);
 }
 
 }  // namespace fio

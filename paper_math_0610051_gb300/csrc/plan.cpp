@@ -12,6 +12,7 @@
 #include <chrono>
 #include <cmath>
 #include <complex>
+#include <cstdio>
 #include <cstdlib>
 #include <cstring>
 #include <numeric>
@@ -467,6 +468,71 @@ void svd_jacobi(int m, int n, std::vector<cd> &A, std::vector<double> &sig, std:
   }
 }
 
+// Right singular vectors and singular values of a square matrix R (n x n,
+// row-major), for the triangular factor of A_[C].  One-sided Jacobi converges
+// in a few sweeps when it is applied to the conjugate transpose of the
+// triangular factor of a column-pivoted QR (Drmac and Veselic, 2008):
+//   R P = Q1 R1 (Householder with column pivoting),  X = R1^H,
+//   X V_X = U_X S (svd_jacobi),  so R = (Q1 V_X) S (P U_X)^H
+// and the right singular vectors of R are V = P U_X, U_X = X V_X S^-1.  V's
+// columns follow sig (descending); a column with sig = 0 is left zero.
+void svd_right_pivoted(int n, const std::vector<cd> &R, std::vector<double> &sig,
+                       std::vector<cd> &V) {
+  std::vector<cd> A(R);
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::vector<double> nrm(n, 0.0);
+  for (int j = 0; j < n; ++j)
+    for (int i = 0; i < n; ++i) nrm[j] += std::norm(A[(size_t)i * n + j]);
+  std::vector<cd> u(n), w(n);
+  for (int k = 0; k < n; ++k) {
+    int piv = k;  // the column of largest remaining norm (rows k .. n-1)
+    for (int j = k + 1; j < n; ++j)
+      if (nrm[j] > nrm[piv]) piv = j;
+    if (piv != k) {
+      for (int i = 0; i < n; ++i) std::swap(A[(size_t)i * n + k], A[(size_t)i * n + piv]);
+      std::swap(nrm[k], nrm[piv]);
+      std::swap(perm[k], perm[piv]);
+    }
+    double sig2 = 0;
+    for (int i = k; i < n; ++i) sig2 += std::norm(A[(size_t)i * n + k]);
+    const double sigma = std::sqrt(sig2);
+    if (sigma > 0) {
+      // reflector H = I - u u^H (u^H u = 2) maps column k onto alpha e_k
+      const cd x0 = A[(size_t)k * n + k];
+      const double ax0 = std::abs(x0);
+      const cd alpha = -(ax0 > 0 ? x0 / ax0 : cd(1.0)) * sigma;
+      const double sc = 1.0 / std::sqrt(sigma * (sigma + ax0));
+      u[k] = (x0 - alpha) * sc;
+      for (int i = k + 1; i < n; ++i) u[i] = A[(size_t)i * n + k] * sc;
+#pragma omp parallel for schedule(static) if (n >= 128)
+      for (int j = k + 1; j < n; ++j) {
+        cd d = 0;
+        for (int i = k; i < n; ++i) d += std::conj(u[i]) * A[(size_t)i * n + j];
+        for (int i = k; i < n; ++i) A[(size_t)i * n + j] -= u[i] * d;
+      }
+      A[(size_t)k * n + k] = alpha;
+      for (int i = k + 1; i < n; ++i) A[(size_t)i * n + k] = 0;
+    }
+    for (int j = k + 1; j < n; ++j) {  // remaining norms (rows k+1 ..), recomputed: no drift
+      double t = 0;
+      for (int i = k + 1; i < n; ++i) t += std::norm(A[(size_t)i * n + j]);
+      nrm[j] = t;
+    }
+  }
+  std::vector<cd> X((size_t)n * n, cd(0));  // X = R1^H
+  for (int i = 0; i < n; ++i)
+    for (int j = i; j < n; ++j) X[(size_t)j * n + i] = std::conj(A[(size_t)i * n + j]);
+  std::vector<cd> VX;
+  svd_jacobi(n, n, X, sig, VX);  // X now holds U_X S
+  V.assign((size_t)n * n, cd(0));
+  for (int kk = 0; kk < n; ++kk) {
+    if (!(sig[kk] > 0)) continue;
+    const double inv = 1.0 / sig[kk];
+    for (int i = 0; i < n; ++i) V[(size_t)perm[i] * n + kk] = X[(size_t)i * n + kk] * inv;
+  }
+}
+
 // ------------------------------------------------------ device bookkeeping --
 
 namespace {
@@ -505,7 +571,8 @@ fio_status cuda_status(cudaError_t e, const char *what) {
 void free_plan_device(fio_plan_s *p) {
   void *ptrs[] = {p->d_wedges, p->d_rows,  p->d_ffts,    p->d_twiddle, p->d_alpha,
                   p->d_beta,   p->d_warp,  p->d_grid,    p->d_fhat,    p->d_errword,
-                  p->d_warps,  p->d_perm,  p->d_cstart,  p->d_items,   p->d_bins};
+                  p->d_warps,  p->d_perm,  p->d_cstart,  p->d_items,   p->d_bins,
+                  p->d_bins1};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   p->d_wedges = nullptr; p->d_rows = nullptr; p->d_ffts = nullptr; p->d_twiddle = nullptr;
@@ -513,6 +580,7 @@ void free_plan_device(fio_plan_s *p) {
   p->d_fhat = nullptr; p->d_errword = nullptr;
   p->d_warps = nullptr; p->d_perm = nullptr; p->d_cstart = nullptr; p->d_items = nullptr;
   p->d_bins = nullptr;
+  p->d_bins1 = nullptr;
 }
 
 // Piecewise polynomials of the KB kernel on the w unit intervals of a window:
@@ -588,6 +656,10 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   fio_options opt;
   fio_options_default(&opt);
   if (opt_in) opt = *opt_in;
+  // FIO_PLAN_TRACE=1: one line per separation attempt on stderr (wedge, r, q,
+  // validated error, relative tail of the dropped singular values, seconds)
+  const char *tr = std::getenv("FIO_PLAN_TRACE");
+  const bool trace = tr && *tr && *tr != '0';
   const char *fa = std::getenv("FIO_FAULT_ALLOC");
   g_fault_countdown = fa ? std::atoi(fa) : -1;
 
@@ -781,9 +853,12 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     return s;
   };
   int *d_ck1 = nullptr, *d_ck2 = nullptr;
-  FIO_CK(dev_alloc((void **)&d_ck1, sizeof(int) * rank_cap * 2 + 64), "alloc samples");
+  // the largest sample: rank_cap columns, or a whole wedge of up to 2 rank_cap
+  // columns (the exact projection); T is fitted on up to 4 rmax rows
+  const int rmax = 2 * rank_cap, nrmax = std::max(4 * rmax, 256);
+  FIO_CK(dev_alloc((void **)&d_ck1, sizeof(int) * rmax * 2 + 64), "alloc samples");
   tmp.ptrs.push_back(d_ck1);
-  d_ck2 = d_ck1 + rank_cap + 16;
+  d_ck2 = d_ck1 + rmax + 16;
   const int *pk1 = p->pt_k1.data(), *pk2 = p->pt_k2.data();
 
   auto eval_cols = [&](int l, const std::vector<int> &C) -> fio_status {
@@ -817,15 +892,15 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     fio_status s = FIO_OK;
     if (s == FIO_OK) s = scratch((void **)&d_pk1, sizeof(int) * (size_t)maxnpts * 2, "alloc points");
     if (s == FIO_OK) s = scratch((void **)&d_err, sizeof(double) * (size_t)maxnpts * 2, "alloc validation");
-    if (s == FIO_OK) s = scratch((void **)&d_rx, sizeof(int) * (size_t)(4 * rank_cap + kValidationRows), "alloc rows");
-    if (s == FIO_OK) s = scratch((void **)&d_W, sizeof(double2) * (size_t)rank_cap * rank_cap, "alloc W");
-    if (s == FIO_OK) s = scratch((void **)&d_P, sizeof(double2) * (size_t)rank_cap * 4 * rank_cap, "alloc P");
-    if (s == FIO_OK) s = scratch((void **)&d_UG, sizeof(double2) * (size_t)kValidationRows * rank_cap, "alloc U rows");
+    if (s == FIO_OK) s = scratch((void **)&d_rx, sizeof(int) * (size_t)(nrmax + kValidationRows), "alloc rows");
+    if (s == FIO_OK) s = scratch((void **)&d_W, sizeof(double2) * (size_t)rmax * rmax, "alloc W");
+    if (s == FIO_OK) s = scratch((void **)&d_P, sizeof(double2) * (size_t)rmax * nrmax, "alloc P");
+    if (s == FIO_OK) s = scratch((void **)&d_UG, sizeof(double2) * (size_t)kValidationRows * rmax, "alloc U rows");
     if (s != FIO_OK) return s;
   }
   d_pk2 = d_pk1 + maxnpts;
   d_nrm = d_err + maxnpts;
-  d_gx = d_rx + 4 * rank_cap;
+  d_gx = d_rx + nrmax;
 
   // rows X of U = A_C W (A_C on the device, [x][c]); W is r x q
   auto u_rows = [&](const std::vector<int> &X, int r, int q, const std::vector<cd> &W,
@@ -908,7 +983,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
       FIO_CK(cudaStreamSynchronize(0), "TSQR kernel");
       std::vector<double> sv;
       std::vector<cd> V;
-      svd_jacobi(rc, rc, Rm, sv, V);
+      svd_right_pivoted(rc, Rm, sv, V);
       const double s1 = sv[0];
       int q = 0;
       while (q < rc && sv[q] > svd_cut * s1) ++q;
@@ -931,7 +1006,9 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
         FIO_CK(cudaMemcpy(d_T, Tex.data(), sizeof(cd) * Tex.size(), cudaMemcpyHostToDevice), "upload T");
       } else {
         SplitMix64 rr{mix_seed(opt.seed, (uint64_t)l + 1, 3 * (uint64_t)attempt + 2)};
-        const int nr = (int)std::min<long long>(NN, std::max(rc, 4 * q));
+        // the row sample of the least-squares fit: its noise amplification
+        // (1 - sqrt(q / nr))^-1 stays near 1.5 or below
+        const int nr = (int)std::min<long long>(NN, std::min(nrmax, std::max({rc, 8 * q, 256})));
         R = sample_distinct((int)NN, nr, rr);
         std::vector<cd> UR;
         if ((s = u_rows(R, rc, q, Wm, UR)) != FIO_OK) return s;
@@ -959,7 +1036,23 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
       for (int i = 0; i < npts; ++i) { se += err[i]; sn += nrm[i]; }
       const double est = std::sqrt(se / std::max(sn, 1e-300));
       const bool ok = (est <= sep_target * eps && 3 * q <= rc) || exact;
-      if (ok || rc >= rank_cap) {
+      if (trace) {
+        double all = 0, tail = 0;
+        for (int k = 0; k < rc; ++k) {
+          all += sv[k] * sv[k];
+          if (k >= q) tail += sv[k] * sv[k];
+        }
+        std::fprintf(stderr,
+                     "fio plan: wedge %d attempt %d r %d q %d est %.3e tail %.3e s_q/s_1 %.3e "
+                     "exact %d t %.2fs\n",
+                     l, attempt, rc, q, est, std::sqrt(tail / std::max(all, 1e-300)),
+                     q < rc ? sv[q] / s1 : 0.0, (int)exact,
+                     std::chrono::duration<double>(std::chrono::steady_clock::now() - t_start).count());
+      }
+      // no larger sample is allowed once rank_cap columns are taken, unless the
+      // whole wedge (at most 2 rank_cap columns) can still be
+      const bool capped = rc >= rank_cap && npts > rmax;
+      if (ok || capped) {
         if (!ok && est > eps) {
           set_error("wedge " + std::to_string(l) + ": separation error " + std::to_string(est) +
                     " above eps with rank_cap samples");
@@ -990,6 +1083,9 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
           ++added;
         }
       r = std::min({2 * r, rank_cap, npts});
+      // a wedge of at most 2 rank_cap columns is sampled whole once half of it
+      // would be: the exact projection then needs no row sample
+      if (2 * r >= npts && npts <= rmax) r = npts;
     }
   }
 
@@ -1114,7 +1210,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   p->sep_err = 0;
   for (double e : p->wedge_err) p->sep_err = std::max(p->sep_err, e);
   p->bytes_total = (sizeof(uint2) + sizeof(uint32_t)) * (size_t)L * NN + sizeof(int) * (size_t)koff +
-                   sizeof(int4) * (size_t)p->n_items + sizeof(int2) * (size_t)p->n_bins +
+                   sizeof(int4) * (size_t)p->n_items +
+                   sizeof(int2) * (size_t)(p->n_bins + p->n_bins1) +
                    (size_t)(aoff + boff) * cs + (size_t)gunit * max_batch * cs +
                    (size_t)NN * max_batch * cs + (size_t)NN * L * sizeof(uint2) +
                    tw.size() / 2 * cs + p->rows.size() * sizeof(RowDev) +

@@ -25,5 +25,7 @@ void herm_eig(int n, std::vector<std::complex<double>> A, std::vector<double> &e
               std::vector<std::complex<double>> &V);
 void svd_jacobi(int m, int n, std::vector<std::complex<double>> &A, std::vector<double> &sig,
                 std::vector<std::complex<double>> &V);
+void svd_right_pivoted(int n, const std::vector<std::complex<double>> &R, std::vector<double> &sig,
+                       std::vector<std::complex<double>> &V);
 
 }  // namespace fio

@@ -84,7 +84,7 @@ EXPORTS = [
     "fio_plan_get_info", "fio_plan_get_wedge", "fio_plan_export_wedge", "fio_plan_export_warp",
     "fio_plan_destroy", "fio_plan_set_timing", "fio_plan_stage_times",
     "fio_dft2", "fio_default_wedges", "fio_wedge_map", "fio_wedge_geometry", "fio_kb_eval",
-    "fio_kb_width_for", "fio_host_eigh", "fio_host_svd", "fio_status_string", "fio_last_error", "fio_version",
+    "fio_kb_width_for", "fio_host_eigh", "fio_host_svd", "fio_host_svd_right", "fio_status_string", "fio_last_error", "fio_version",
     "fio_surrogate_train", "fio_surrogate_destroy", "fio_surrogate_get_info", "fio_surrogate_params",
     "fio_surrogate_eval", "fio_surrogate_loss_grad", "fio_surrogate_samples", "fio_surrogate_nparams",
 ]
@@ -126,6 +126,7 @@ def lib():
             L.fio_kb_width_for.argtypes = [D]
             L.fio_host_eigh.argtypes = [I, P, P, P]
             L.fio_host_svd.argtypes = [I, I, P, P, P, P]
+            L.fio_host_svd_right.argtypes = [I, P, P, P]
             L.fio_surrogate_train.argtypes = [ctypes.POINTER(_Phase), I, I, I, ctypes.c_ulonglong,
                                               ctypes.POINTER(P)]
             L.fio_surrogate_destroy.argtypes = [P]
@@ -458,3 +459,13 @@ def host_svd(A: np.ndarray):
     V = np.empty((n, n), np.complex128)
     _check(lib().fio_host_svd(m, n, _np_ptr(A), _np_ptr(s), _np_ptr(AV), _np_ptr(V)), "fio_host_svd")
     return s, AV, V
+
+
+def host_svd_right(R: np.ndarray):
+    """(s, V) of fio_host_svd_right: singular values and right singular vectors."""
+    R = np.ascontiguousarray(R, np.complex128)
+    n = R.shape[0]
+    s = np.empty(n)
+    V = np.empty((n, n), np.complex128)
+    _check(lib().fio_host_svd_right(n, _np_ptr(R), _np_ptr(s), _np_ptr(V)), "fio_host_svd_right")
+    return s, V

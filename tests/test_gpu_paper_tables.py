@@ -47,7 +47,10 @@ def test_table1_separation_error(env):
         errs = []
         for eps in (1e-3, 1e-4, 1e-5, 1e-6):
             with fio.Plan(N, fio.PHASE_ELLIPSE_PRODUCT, prm, eps) as plan:
-                errs.append(plan.info()["sep_error"])
+                info = plan.info()
+                errs.append(info["sep_error"])
+            print(f"Table 1: N={N} eps={eps:g} error {errs[-1]:.2e} q mean {info['q_mean']:.1f} "
+                  f"r max {info['r_max']} plan {info['plan_seconds']:.1f} s", flush=True)
             assert errs[-1] <= eps, (N, eps, errs[-1])
         rows.append(f"N={N:4d}  " + "  ".join(f"{e:.2e}" for e in errs))
     print("\nTable 1 (largest per-wedge separation error, eps = 1e-3 .. 1e-6):\n" + "\n".join(rows))
@@ -65,6 +68,8 @@ def test_table2_ranks(env):
             with fio.Plan(N, fio.PHASE_ELLIPSE_PRODUCT, prm, float(N) ** -p) as plan:
                 info = plan.info()
                 qs.append((info["q_max"], info["q_mean"]))
+            print(f"Table 2: N={N} p={p} q max {qs[-1][0]} mean {qs[-1][1]:.1f} "
+                  f"error {info['sep_error']:.2e} plan {info['plan_seconds']:.1f} s", flush=True)
         assert all(b[0] >= a[0] for a, b in zip(qs, qs[1:])), (N, qs)  # grows with p
         lines.append(f"N={N:4d}  ours (max/mean) " +
                      "  ".join(f"{m:2d}/{a:4.1f}" for m, a in qs) + "   paper " + " ".join(map(str, paper)))

@@ -151,12 +151,14 @@ def test_tau_modes_amplitude_batch(env, orc):
         one = plan.apply(x[5:6].clone()).cpu().numpy()
         adj = plan.adjoint(x).cpu().numpy()
         adj_one = plan.adjoint(x[5:6].clone()).cpu().numpy()
+        adj_again = plan.adjoint(x).cpu().numpy()
         plan.sync()
-    # Batching does not change the arithmetic. The forward sum over wedges is an
-    # atomic add, so its order (and the last float32 bit) may differ between runs;
-    # the adjoint has no atomics and is bit-identical.
+    # Batching changes only the order of the sums: the forward sum over wedges is
+    # an atomic add, and the spread's lane layout depends on how many channels a
+    # grid cell holds.  The adjoint has no atomics: a repeated call is bit-identical.
     assert rel(out[5], one[0]) < 1e-6
-    assert np.array_equal(adj_one[0], adj[5])
+    assert rel(adj[5], adj_one[0]) < 1e-6
+    assert np.array_equal(adj, adj_again)
     ph, amp = orc.Phase(orc.TAU_MODES, prm), orc.Amplitude(1, 0.5, 0.3)
     n1, n2 = synth.sample_points(N, 256, seed=2)
     for b in (0, 7):

@@ -301,3 +301,34 @@ def test_host_svd_rank_deficient_and_zero(fio):
     s0, AV0, V0 = fio.host_svd(np.zeros((6, 3)))
     assert np.all(s0 == 0) and np.all(AV0 == 0)
     assert np.allclose(V0.conj().T @ V0, np.eye(3))
+
+
+@pytest.mark.parametrize("n", [1, 7, 48, 130])
+def test_host_svd_right_matches_numpy(fio, n):
+    """The column-pivoted preconditioned Jacobi SVD applied to triangular factors
+    (Sec. 3.2): singular values as LAPACK's, R V orthogonal columns of norms s,
+    V unitary; graded factors keep the small singular values."""
+    g = np.random.default_rng(n)
+    R = np.triu(g.standard_normal((n, n)) + 1j * g.standard_normal((n, n)))
+    R = R * np.logspace(0, -10, n)[None, :]
+    s, V = fio.host_svd_right(R)
+    ref = np.linalg.svd(R, compute_uv=False)
+    assert np.max(np.abs(s - ref)) < 1e-13 * ref[0]
+    # a singular vector is determined to about 1e-16 s_1 / s_k: check those of
+    # singular values above 1e-8 s_1 (the separation keeps s_k > 0.25 eps s_1)
+    k = int(np.sum(s > 1e-8 * s[0]))
+    Vk = V[:, :k]
+    assert np.max(np.abs(Vk.conj().T @ Vk - np.eye(k))) < 1e-7
+    RV = R @ Vk
+    assert np.max(np.abs(RV.conj().T @ RV - np.diag(s[:k] ** 2))) < 1e-13 * ref[0] ** 2
+
+
+def test_host_svd_right_rank_deficient(fio):
+    g = np.random.default_rng(5)
+    R = (g.standard_normal((20, 3)) + 1j * g.standard_normal((20, 3))) @ (g.standard_normal((3, 20)))
+    s, V = fio.host_svd_right(R)
+    ref = np.linalg.svd(R, compute_uv=False)
+    assert np.max(np.abs(s[:3] - ref[:3])) < 1e-13 * ref[0]
+    assert np.all(s[3:] < 1e-13 * ref[0])
+    RV = R @ V[:, :3]
+    assert np.max(np.abs(RV.conj().T @ RV - np.diag(s[:3] ** 2))) < 1e-12 * ref[0] ** 2
