@@ -105,7 +105,7 @@ typedef struct {
   int kb_width;               /* Kaiser-Bessel width in grid cells; 0 = ceil(log10(45/eps)) */
   unsigned long long seed;    /* seed of the random column/row samples of Sec. 3.2 */
   int r0;                     /* initial sample count r; 0 = 8 */
-  int rank_cap;               /* largest r before FIO_ERANK; 0 = 512 */
+  int rank_cap;               /* largest r before FIO_ERANK; 0 = 1024 */
   int max_batch;              /* largest batch the plan's workspace holds; 0 = 1 */
   fio_surrogate surrogate;    /* trained phase surrogate (tau-mode phases), or NULL; see below */
   double surrogate_warp_budget; /* largest judged warp error, in cycles at |xi| = N/sqrt 2, for
@@ -329,6 +329,23 @@ fio_status fio_plan_export_wedge(fio_plan plan, int l, double *alpha, double *be
 fio_status fio_plan_export_warp(fio_plan plan, int l, double *y);
 
 void fio_plan_destroy(fio_plan plan);
+
+/* Write the plan to the file `path` (host path), so that fio_plan_load can
+ * rebuild it without repeating the preprocessing of Sec. 3.2: the factors
+ * alpha' and beta', the warped points, the point order, the wedge tables and the
+ * work lists, as the plan holds them (about bytes_total minus the workspace).
+ * Synchronises the device.  FIO_EINVAL if the file cannot be opened, FIO_ECUDA
+ * if a copy or a write fails. */
+fio_status fio_plan_save(fio_plan plan, const char *path);
+
+/* Rebuild a plan saved by fio_plan_save, on the current device.  max_batch > 0
+ * sizes the new workspace (0 = the saved plan's).  The loaded plan applies the
+ * same operator with the same arithmetic as the saved one.  FIO_EINVAL for a
+ * missing file, a file of another format or version, or a corrupt or truncated
+ * file (checked before any device allocation where the header tells);
+ * FIO_ENOMEM if the device allocations fail.  On failure *out_plan = NULL and
+ * nothing leaks. */
+fio_status fio_plan_load(const char *path, int max_batch, fio_plan *out_plan);
 
 /* Unitary 2D DFT of Eq. dft (inverse = 0) or its inverse (inverse = 1) on the
  * GPU, spectrum in centred order.  in/out: device arrays of batch*N*N complex

@@ -104,6 +104,45 @@ void fio_plan_destroy(fio_plan p) {
   delete p;
 }
 
+fio_status fio_plan_save(fio_plan p, const char *path) {
+  if (!plan_ok(p) || !path) {
+    set_error("fio_plan_save: invalid plan or path");
+    return FIO_EINVAL;
+  }
+  if (cudaDeviceSynchronize() != cudaSuccess) {
+    set_error("fio_plan_save: pending CUDA error");
+    return FIO_ECUDA;
+  }
+  return save_plan(p, path);
+}
+
+fio_status fio_plan_load(const char *path, int max_batch, fio_plan *out_plan) {
+  if (!out_plan || !path || max_batch < 0 || max_batch > 4096) {
+    set_error("fio_plan_load: bad arguments");
+    return FIO_EINVAL;
+  }
+  *out_plan = nullptr;
+  fio_plan_s *p = new (std::nothrow) fio_plan_s();
+  if (!p) {
+    set_error("host allocation failed");
+    return FIO_ENOMEM;
+  }
+  fio_status s;
+  try {
+    s = load_plan(p, path, max_batch);
+  } catch (const std::bad_alloc &) {
+    set_error("host allocation failed");
+    s = FIO_ENOMEM;
+  }
+  if (s != FIO_OK) {
+    free_plan_device(p);
+    delete p;
+    return s;
+  }
+  *out_plan = p;
+  return FIO_OK;
+}
+
 fio_status fio_apply(fio_plan p, const void *f, void *out, int batch, void *stream) {
   if (!plan_ok(p)) return FIO_EINVAL;
   if (!f || !out || f == out || batch < 1 || batch > p->max_batch) {

@@ -104,6 +104,8 @@ struct fio_plan_s {
   std::vector<int> pt_k1, pt_k2;   // every frequency, wedge by wedge, row-major in each box
   long long grid_units = 0;        // sum_l m1 m2 q
   long long alpha_elems = 0, beta_elems = 0;
+  long long cstart_elems = 0;      // entries of all bucket tables
+  long long twiddle_elems = 0;     // complex entries of the twiddle tables
   int max_row_len = 0;
 
   // device arrays
@@ -144,6 +146,10 @@ namespace fio {
 
 // Thread-local error text (api.cpp).
 void set_error(const std::string &msg);
+
+// plan_io.cpp: the plan file of fio_plan_save / fio_plan_load
+fio_status save_plan(const fio_plan_s *p, const char *path);
+fio_status load_plan(fio_plan_s *p, const char *path, int max_batch);
 
 // plan.cpp
 fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_amplitude *amp,

@@ -697,7 +697,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   const int w = opt.kb_width > 0 ? opt.kb_width : kb_width_for(eps);
   if (w < 3 || w > kMaxKbWidth) { set_error("kb_width must lie in [3, 12]"); return FIO_EINVAL; }
   const int r0 = opt.r0 > 0 ? opt.r0 : 8;
-  const int rank_cap = opt.rank_cap > 0 ? opt.rank_cap : 512;
+  const int rank_cap = opt.rank_cap > 0 ? opt.rank_cap : 1024;
   const int max_batch = opt.max_batch > 0 ? opt.max_batch : 1;
   if (max_batch > 4096) { set_error("max_batch too large"); return FIO_EINVAL; }
   if (!(opt.sep_cut >= 0 && opt.sep_cut <= 1) || !(opt.sep_target >= 0 && opt.sep_target <= 1)) {
@@ -1112,6 +1112,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     koff += (long long)wd.nb1 * wd.nb2 * kBin * kBin + 1;
   }
   p->alpha_elems = aoff;
+  p->cstart_elems = koff;
+  p->twiddle_elems = (long long)tw.size() / 2;
   p->beta_elems = boff;
   p->grid_units = gunit;
   FIO_CK(dev_alloc(&p->d_alpha, (size_t)aoff * cs), "alloc alpha");

@@ -82,7 +82,7 @@ EXPORTS = [
     "fio_apply_noalloc",
     "fio_plan_sync",
     "fio_plan_get_info", "fio_plan_get_wedge", "fio_plan_export_wedge", "fio_plan_export_warp",
-    "fio_plan_destroy", "fio_plan_set_timing", "fio_plan_stage_times",
+    "fio_plan_destroy", "fio_plan_set_timing", "fio_plan_stage_times", "fio_plan_save", "fio_plan_load",
     "fio_dft2", "fio_default_wedges", "fio_wedge_map", "fio_wedge_geometry", "fio_kb_eval",
     "fio_kb_width_for", "fio_host_eigh", "fio_host_svd", "fio_host_svd_right", "fio_status_string", "fio_last_error", "fio_version",
     "fio_surrogate_train", "fio_surrogate_destroy", "fio_surrogate_get_info", "fio_surrogate_params",
@@ -117,6 +117,8 @@ def lib():
             L.fio_plan_set_timing.argtypes = [P, I]
             L.fio_plan_stage_times.argtypes = [P, P, P]
             L.fio_plan_destroy.argtypes = [P]
+            L.fio_plan_save.argtypes = [P, ctypes.c_char_p]
+            L.fio_plan_load.argtypes = [ctypes.c_char_p, I, P]
             L.fio_plan_destroy.restype = None
             L.fio_dft2.argtypes = [I, I, P, P, I, I, P]
             L.fio_default_wedges.argtypes = [I]
@@ -208,6 +210,29 @@ class Plan:
                                          ctypes.byref(opt), ctypes.byref(self._handle)),
                    "fio_plan_create")
         self.dtype = torch.complex128 if self.precision == FP64 else torch.complex64
+
+    # -- files
+    def save(self, path: str):
+        """fio_plan_save: write the plan to `path`."""
+        with self._torch.cuda.device(self.device):
+            _check(lib().fio_plan_save(self._handle, os.fsencode(path)), "fio_plan_save")
+
+    @classmethod
+    def load(cls, path: str, max_batch: int = 0, device=None) -> "Plan":
+        """fio_plan_load: a plan rebuilt from `path` on `device` (default: current)."""
+        import torch
+        self = cls.__new__(cls)
+        self._torch = torch
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
+        self._handle = ctypes.c_void_p()
+        self._surrogate = None
+        with torch.cuda.device(self.device):
+            _check(lib().fio_plan_load(os.fsencode(path), int(max_batch), ctypes.byref(self._handle)),
+                   "fio_plan_load")
+        info = self.info()
+        self.N, self.precision, self.max_batch = info["N"], info["precision"], info["max_batch"]
+        self.dtype = torch.complex128 if self.precision == FP64 else torch.complex64
+        return self
 
     # -- lifetime
     def close(self):

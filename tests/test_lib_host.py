@@ -332,3 +332,21 @@ def test_host_svd_right_rank_deficient(fio):
     assert np.all(s[3:] < 1e-13 * ref[0])
     RV = R @ V[:, :3]
     assert np.max(np.abs(RV.conj().T @ RV - np.diag(s[:3] ** 2))) < 1e-12 * ref[0] ** 2
+
+
+def test_plan_load_rejects_bad_files_without_a_gpu(fio, tmp_path):
+    """fio_plan_load reads and checks the file's header before any CUDA call: a
+    missing file, a foreign file and a plan file of a truncated header are
+    FIO_EINVAL, and no plan is returned."""
+    lib = fio.lib()
+    bad = os.path.join(tmp_path, "bad.fioplan")
+    with open(bad, "wb") as fh:
+        fh.write(b"NOTAPLAN" + bytes(64))
+    short = os.path.join(tmp_path, "short.fioplan")
+    with open(short, "wb") as fh:
+        fh.write(b"FIOPLAN1" + (1).to_bytes(4, "little"))
+    for path in (bad, short, os.path.join(tmp_path, "missing.fioplan")):
+        h = ctypes.c_void_p(1)
+        assert lib.fio_plan_load(os.fsencode(path), 0, ctypes.byref(h)) == fio.FIO_EINVAL
+        assert not h.value
+        assert b"fio_plan_load" in lib.fio_last_error()
