@@ -154,13 +154,14 @@ k_scatter_rowfft(const Cx<T> *__restrict__ fhat, const WedgeDev *__restrict__ W,
       const int k2pp = x2p + w.xc2;
       const int k1 = w.Minv[0] * k1pp + w.Minv[1] * k2pp;
       const int k2 = w.Minv[2] * k1pp + w.Minv[3] * k2pp;
-      const size_t idx = (size_t)imodp(k1, N) * N + imodp(k2, N);
-      a[imodp(x2p, n) * nlc + lm.l] = cmul(bt[j], fb[idx]);
+      // k1, k2 in [-N/2, N/2) and x2p in (-n, n): one conditional add each
+      const size_t idx = (size_t)(k1 < 0 ? k1 + N : k1) * N + (k2 < 0 ? k2 + N : k2);
+      a[(x2p < 0 ? x2p + n : x2p) * nlc + lm.l] = cmul(bt[j], fb[idx]);
     }
   }
   __syncthreads();
-  fft_exec_dif(a, n, nlc, pl, +1, tw);
-  C *out = grid + w.grid_unit * B + (long long)imodp(rw.xi1, w.m1) * n * nch + c0;
+  fft_exec_dif<+1>(a, n, nlc, pl, tw);
+  C *out = grid + w.grid_unit * B + (long long)(rw.xi1 < 0 ? rw.xi1 + w.m1 : rw.xi1) * n * nch + c0;
   if ((int)threadIdx.x < lm.lanes)
     for (int e = lm.i0; e < n; e += lm.step) out[(long long)e * nch + lm.l] = a[pos[e] * nlc + lm.l];
 }
@@ -170,23 +171,29 @@ k_scatter_rowfft(const Cx<T> *__restrict__ fhat, const WedgeDev *__restrict__ W,
 // of the flattened [g2][ch] dimension of one wedge.  adjoint = 0: input rows
 // outside the box are zero (not read), all m1 outputs written, exp(+2 pi i).
 // adjoint = 1: all rows read, only box rows written, exp(-2 pi i).
+// First column block of every wedge (a prefix sum over the wedges, made on the
+// host for the launch's batch): the CTA finds its wedge by binary search.
+struct ColBlocks {
+  int L;
+  int start[kMaxWedges + 1];
+};
+
 template <typename T>
 __global__ void __launch_bounds__(kFftThreads)
 k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
-         const FftPlanDev *__restrict__ ffts, const Cx<T> *__restrict__ tw_all, int L, int B,
-         int adjoint) {
+         const FftPlanDev *__restrict__ ffts, const Cx<T> *__restrict__ tw_all,
+         const ColBlocks cb, int B, int adjoint) {
   using C = Cx<T>;
   extern __shared__ unsigned char smem_raw[];
-  // locate (wedge, chunk) for this block
-  int blk = blockIdx.x, l = 0, nl = 1;
-  for (; l < L; ++l) {
-    nl = fft_lines(W[l].m1, prec_of<T>());
-    const int cnt = (W[l].m2 * B * W[l].qp + nl - 1) / nl;
-    if (blk < cnt) break;
-    blk -= cnt;
+  int lo = 0, hi = cb.L - 1;  // the wedge with start[l] <= blockIdx.x < start[l + 1]
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cb.start[mid] <= (int)blockIdx.x) lo = mid;
+    else hi = mid - 1;
   }
-  if (l >= L) return;
+  const int l = lo, blk = blockIdx.x - cb.start[l];
   const WedgeDev w = W[l];
+  const int nl = fft_lines(w.m1, prec_of<T>());
   const int nch = B * w.qp;
   const long long rs = (long long)w.m2 * nch;  // row stride
   const long long cc0 = (long long)blk * nl;
@@ -207,7 +214,8 @@ k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
     __syncthreads();
     if (on)
       for (int e = lm.i0; e < w.n1; e += lm.step) {
-        const int g1 = imodp(w.b1 + e, n);
+        int g1 = w.b1 + e;  // box row, -n < g1 < n
+        if (g1 < 0) g1 += n;
         cp_async_elem(&a[g1 * nlc + c], &g[g1 * rs + c]);
       }
   } else if (on) {
@@ -215,13 +223,15 @@ k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
   }
   cp_async_wait();
   __syncthreads();
-  fft_exec_dif(a, n, nlc, pl, adjoint ? -1 : +1, tw);
+  if (adjoint) fft_exec_dif<-1>(a, n, nlc, pl, tw);
+  else fft_exec_dif<+1>(a, n, nlc, pl, tw);
   if (!on) return;
   if (!adjoint) {
     for (int e = lm.i0; e < n; e += lm.step) g[e * rs + c] = a[pos[e] * nlc + c];
   } else {
     for (int e = lm.i0; e < w.n1; e += lm.step) {
-      const int g1 = imodp(w.b1 + e, n);
+      int g1 = w.b1 + e;
+      if (g1 < 0) g1 += n;
       g[g1 * rs + c] = a[pos[g1] * nlc + c];
     }
   }
@@ -259,7 +269,7 @@ k_rowfft_adj(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
       cp_async_elem(&a[e * nlc + lm.l], &row[(long long)e * nch + lm.l]);
   cp_async_wait();
   __syncthreads();
-  fft_exec_dif(a, n, nlc, pl, -1, tw);
+  fft_exec_dif<-1>(a, n, nlc, pl, tw);
   if (on)
     for (int j = lm.i0; j < rw.len; j += lm.step) {
       const int g2 = imodp(rw.a + j, n);
@@ -348,6 +358,7 @@ cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int bat
 struct LaunchGeom {
   int max_m1 = 0, max_m2 = 0, max_q = 0, col_blocks = 0, row_chunks = 0;
   size_t smem_col = 0, smem_row = 0;
+  ColBlocks cb{};
 };
 
 // Launch shapes of the in-place line FFTs: column blocks, row-chunk count and
@@ -361,6 +372,7 @@ static LaunchGeom geom(const fio_plan_s *p, int B) {
     g.max_m2 = std::max(g.max_m2, w.m2);
     g.max_q = std::max(g.max_q, w.qp);
     const int nl1 = fft_lines(w.m1, prec), nl2 = fft_lines(w.m2, prec);
+    g.cb.start[g.cb.L++] = g.col_blocks;
     g.col_blocks += (w.m2 * B * w.qp + nl1 - 1) / nl1;
     g.row_chunks = std::max(g.row_chunks, (B * w.qp + nl2 - 1) / nl2);
     g.smem_col = std::max(g.smem_col, ((size_t)w.m1 * nl1 + w.m1) * cs + ((size_t)w.m1 * 2 + 15) / 16 * 16);
@@ -443,7 +455,7 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
   {
     StageTimer st(p, s, FIO_STAGE_S2_COLFFT, timing);
     k_colfft<T><<<g0.col_blocks, kFftThreads, g0.smem_col, s>>>((C *)grid_ws, p->d_wedges, p->d_ffts,
-                                                            (const C *)p->d_twiddle, L, B, 0);
+                                                            (const C *)p->d_twiddle, g0.cb, B, 0);
     p->launches += 1;
   }
   // S3
@@ -476,7 +488,7 @@ static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out,
     StageTimer st(p, s, FIO_STAGE_S4B_COLFFT);
     k_colfft<T><<<g0.col_blocks, kFftThreads, g0.smem_col, s>>>((C *)p->d_grid, p->d_wedges,
                                                             p->d_ffts, (const C *)p->d_twiddle,
-                                                            L, B, 1);
+                                                            g0.cb, B, 1);
     p->launches += 1;
   }
   // S4b rows

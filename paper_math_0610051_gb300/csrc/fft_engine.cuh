@@ -75,10 +75,9 @@ __device__ __forceinline__ float2 fsub2(float2 a, float2 b) {
 }
 template <> __device__ __forceinline__ float2 cadd<float2>(float2 a, float2 b) { return fadd2(a, b); }
 template <> __device__ __forceinline__ float2 csub<float2>(float2 a, float2 b) { return fsub2(a, b); }
-// (a.x b.x - a.y b.y, a.x b.y + a.y b.x) = (a.x, a.x) (b.x, b.y) + (-a.y, a.y) (b.y, b.x)
-template <> __device__ __forceinline__ float2 cmul<float2>(float2 a, float2 b) {
-  return ffma2(make_float2(-a.y, a.y), make_float2(b.y, b.x), fmul2(make_float2(a.x, a.x), b));
-}
+// The complex product stays scalar (two FMUL, two FFMA): a packed form needs the
+// operands swizzled, (a.x, a.x), (-a.y, a.y), (b.y, b.x), which costs more ALU
+// moves than it saves.
 
 // ---------------------------------------------------------------- butterflies
 // V[k] = sum_r v[r] exp(sign 2 pi i r k / R)
@@ -254,9 +253,10 @@ __device__ __forceinline__ LineMap line_map(int nl) {
 // and writes it back to a[j + k m/R]: every butterfly reads and writes the same
 // R slots, so one buffer and one barrier per stage suffice.  The result is in
 // digit-reversed order: frequency k is at fft_dif_pos(k).
-template <int R, typename C>
-__device__ __forceinline__ void fft_stage_dif(C *a, int n, int nl, int m, int sign,
+template <int R, int SIGN, typename C>
+__device__ __forceinline__ void fft_stage_dif(C *a, int n, int nl, int m,
                                               const C *__restrict__ tw, const LineMap &lm) {
+  constexpr int sign = SIGN;
   if ((int)threadIdx.x >= lm.lanes) return;
   const int mr = m / R;          // butterfly stride within a block
   const int tws = n / m;         // table step of exp(sign 2 pi i / m)
@@ -291,19 +291,20 @@ __device__ __forceinline__ void fft_stage_dif(C *a, int n, int nl, int m, int si
 }
 
 // Run all stages of plan `pl` in place on a (nl interleaved lines: element e of
-// line l at a[e nl + l]).  Call after a barrier; ends with a barrier.
-template <typename C>
-__device__ void fft_exec_dif(C *a, int n, int nl, const FftPlanDev &pl, int sign, const C *tw) {
+// line l at a[e nl + l]), transform sign SIGN (compile time).  Call after a
+// barrier; ends with a barrier.
+template <int SIGN, typename C>
+__device__ void fft_exec_dif(C *a, int n, int nl, const FftPlanDev &pl, const C *tw) {
   const LineMap lm = line_map(nl);
   int m = n;
   for (int s = 0; s < pl.nstages; ++s) {
     const int R = pl.radix[s];
     switch (R) {
-      case 8: fft_stage_dif<8>(a, n, nl, m, sign, tw, lm); break;
-      case 4: fft_stage_dif<4>(a, n, nl, m, sign, tw, lm); break;
-      case 2: fft_stage_dif<2>(a, n, nl, m, sign, tw, lm); break;
-      case 3: fft_stage_dif<3>(a, n, nl, m, sign, tw, lm); break;
-      case 5: fft_stage_dif<5>(a, n, nl, m, sign, tw, lm); break;
+      case 8: fft_stage_dif<8, SIGN>(a, n, nl, m, tw, lm); break;
+      case 4: fft_stage_dif<4, SIGN>(a, n, nl, m, tw, lm); break;
+      case 2: fft_stage_dif<2, SIGN>(a, n, nl, m, tw, lm); break;
+      case 3: fft_stage_dif<3, SIGN>(a, n, nl, m, tw, lm); break;
+      case 5: fft_stage_dif<5, SIGN>(a, n, nl, m, tw, lm); break;
     }
     __syncthreads();
     m /= R;

@@ -12,6 +12,7 @@
 namespace fio {
 
 constexpr int kMaxRadixStages = 16;
+constexpr int kMaxWedges = 256;  // largest L a plan accepts
 constexpr int kMaxFftLen = 4096;
 constexpr int kMaxKbWidth = 12;
 constexpr int kMaxHornerDeg = 15;

@@ -595,6 +595,12 @@ cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int 
 
 cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s) {
   if (p->precision == FIO_FP64) return dispatch_w<double>(p, g, grid, nullptr, B, true, s);
+  // one lane per channel pays when a cell holds more than 32 channels (several
+  // inputs); a single input takes the bin-pair kernel, whose lane groups own a
+  // column each
+  int qpmax = 2;
+  for (const WedgeDev &w : p->wedges) qpmax = std::max(qpmax, w.qp);
+  if (B * qpmax <= 32) return dispatch_w<float>(p, g, grid, nullptr, B, true, s);
   return launch_spread_sweep(p, g, grid, B, s);
 }
 

@@ -693,7 +693,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   if (opt.precision != FIO_MIXED && opt.precision != FIO_FP64) { set_error("invalid precision"); return FIO_EINVAL; }
   const int L = opt.L > 0 ? opt.L : default_L(N);
   const double sigma = opt.sigma > 0 ? opt.sigma : 2.0;
-  if (L < 1 || L > 256 || sigma < 1.25 || sigma > 4.0) { set_error("L or sigma out of range"); return FIO_EINVAL; }
+  if (L < 1 || L > kMaxWedges || sigma < 1.25 || sigma > 4.0) { set_error("L or sigma out of range"); return FIO_EINVAL; }
   const int w = opt.kb_width > 0 ? opt.kb_width : kb_width_for(eps);
   if (w < 3 || w > kMaxKbWidth) { set_error("kb_width must lie in [3, 12]"); return FIO_EINVAL; }
   const int r0 = opt.r0 > 0 ? opt.r0 : 8;

@@ -12,10 +12,10 @@
 // Warp c owns cell column c of the bin.  Its lanes cover the channels of a cell,
 // ch = b qp + t (input b, rank term t), the grid's innermost dimension, so every
 // lane of a warp walks the same sequence of points and reads the same weights:
-//   - large batches: a lane holds UPL single-term units, ch = lane + 32 j;
-//   - small batches (B qp <= 32): a unit holds two terms and the warp splits into
-//     G = 32 / (B qp / 2) lane groups that share the column and take the points
-//     in turn; their sums are added by shuffles when a cell row is complete.
+// a lane holds UPL single-term units, ch = lane + 32 j.  This layout serves
+// launches whose cells hold more than 32 channels (several inputs); a single
+// input takes the bin-pair kernel k_spread_bin, whose lane groups own one column
+// each.
 // The warp walks the region's start rows top to bottom, keeping in registers the
 // w cell rows that the current start row can still reach: a point of start row i
 // and start column j (w - 1 or fewer columns left of the cell column) adds
@@ -51,20 +51,7 @@ constexpr int kSwMaxChunk = 512;
 // Registers: a lane keeps w x UPL accumulators of two floats; at most 30 of them.
 __host__ __device__ constexpr int max_upl(int W) { return 30 / W < 1 ? 1 : (30 / W > 8 ? 8 : 30 / W); }
 
-__device__ __forceinline__ float4 uadd(float4 a, float4 b) {
-  const float2 lo = fadd2(make_float2(a.x, a.y), make_float2(b.x, b.y));
-  const float2 hi = fadd2(make_float2(a.z, a.w), make_float2(b.z, b.w));
-  return make_float4(lo.x, lo.y, hi.x, hi.y);
-}
-template <typename U> __device__ __forceinline__ U zero_unit();
-template <> __device__ __forceinline__ float2 zero_unit<float2>() { return make_float2(0.f, 0.f); }
-template <> __device__ __forceinline__ float4 zero_unit<float4>() {
-  return make_float4(0.f, 0.f, 0.f, 0.f);
-}
-__device__ __forceinline__ float4 shfl_unit(float4 v, int src) {
-  return make_float4(__shfl_sync(kFull, v.x, src), __shfl_sync(kFull, v.y, src),
-                     __shfl_sync(kFull, v.z, src), __shfl_sync(kFull, v.w, src));
-}
+__device__ __forceinline__ float2 zero_unit() { return make_float2(0.f, 0.f); }
 
 // Per-chunk shared arrays: weights [kc][2W] floats, sorted position and output
 // index [kc] ints, start column [kc] bytes, then v [kc][chp], the staged alpha'
@@ -73,7 +60,7 @@ __host__ __device__ constexpr size_t sw_meta_bytes(int kc, int W) {
   return ((size_t)kc * (2 * W * 4 + 4 + 4 + 1) + 15) / 16 * 16;
 }
 
-template <int W, int UPL, bool PAIR>
+template <int W, int UPL>
 __global__ void __launch_bounds__(kSwThreads, 1)
 k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
                const WedgeDev *__restrict__ Wd, const int2 *__restrict__ bins,
@@ -81,9 +68,7 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
                const uint2 *__restrict__ warps, const uint32_t *__restrict__ perm, long long NN,
                int B, KbDev kb, HornerDev hz, int kc, int chp, int qpmax, int nbmax,
                int *errw) {
-  using U = std::conditional_t<PAIR, float4, float2>;  // a unit: two terms or one
-  constexpr int S = PAIR ? 2 : 1;
-  static_assert(!PAIR || UPL == 1, "paired units use one unit per lane");
+  using U = float2;  // a unit: one complex term
   __shared__ int sRS[kSwRegion + 1];  // region-ordered first candidate of every start cell
   __shared__ int sGB[kSwRegion];      // sorted position of every start cell's first point
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -145,22 +130,16 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
   const FastDiv dqp = make_fastdiv((unsigned)qp);
 
   for (int ch0 = 0; ch0 < nch; ch0 += chp) {
-    const int npc = min(chp, nch - ch0);  // channels of this pass (even when PAIR)
-    const int nu = npc / S;               // units of this pass
+    const int npc = min(chp, nch - ch0);  // channels of this pass
+    const int nu = npc;                   // units of this pass
     const FastDiv dnpc = make_fastdiv((unsigned)npc);
     const int b_lo = ch0 / qp, nbp = (ch0 + npc - 1) / qp - b_lo + 1;  // inputs of the pass
-    int G = 1, g = 0, k = lane;           // lane groups, this lane's group and unit
-    if (PAIR) {
-      G = 32 / nu;
-      g = lane / nu;
-      k = lane - g * nu;
-    }
-    const bool lane_on = g < G;
+    const int k = lane;  // this lane's first unit
     U acc[W][UPL];
 #pragma unroll
     for (int a = 0; a < W; ++a)
 #pragma unroll
-      for (int j = 0; j < UPL; ++j) acc[a][j] = zero_unit<U>();
+      for (int j = 0; j < UPL; ++j) acc[a][j] = zero_unit();
     int i = 0;  // next start row of the sweep
     for (int ch = 0; ch < nchunks; ++ch) {
       const int c = ch * kc;
@@ -208,9 +187,8 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
         const int rb = i * RW + cl;
         const int end = sRS[rb + W];
         const int lo = max(sRS[rb] - c, 0), hi = min(end - c, np);
-        if (lane_on) {
-          // this group's points of the row segment: lo + g, lo + g + G, ...
-          for (int t = lo + g; t < hi; t += G) {
+        {
+          for (int t = lo; t < hi; ++t) {
             const float *wr = sWt[t];
             const float w2 = wr[W + (cl + W - 1 - sCol[t])];
             float w1[W];
@@ -232,7 +210,7 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
 #pragma unroll
             for (int j = 0; j < UPL; ++j) {
               const int u = k + 32 * j;
-              v[j] = (PAIR || u < nu) ? sVu[t * nu + u] : zero_unit<U>();
+              v[j] = u < nu ? sVu[t * nu + u] : zero_unit();
               uscale(v[j], w2);
             }
 #pragma unroll
@@ -244,34 +222,27 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
         if (end > c + np) break;  // the start row continues in the next chunk
         // start row i is complete: cell row i - (W - 1) is final
         const int rl = i - (W - 1);
-        if constexpr (PAIR) {
-          U sum = acc[0][0];
-          for (int gg = 1; gg < G; ++gg) sum = uadd(sum, shfl_unit(acc[0][0], lane + gg * nu));
-          if (rl >= 0 && g == 0)
-            reinterpret_cast<U *>(gw + ((long long)(r0 + rl) * m2 + c0 + cl) * nch + ch0)[k] = sum;
-        } else {
-          if (rl >= 0) {
-            U *dst = reinterpret_cast<U *>(gw + ((long long)(r0 + rl) * m2 + c0 + cl) * nch + ch0);
+        if (rl >= 0) {
+          U *dst = reinterpret_cast<U *>(gw + ((long long)(r0 + rl) * m2 + c0 + cl) * nch + ch0);
 #pragma unroll
-            for (int j = 0; j < UPL; ++j)
-              if (k + 32 * j < nu) dst[k + 32 * j] = acc[0][j];
-          }
+          for (int j = 0; j < UPL; ++j)
+            if (k + 32 * j < nu) dst[k + 32 * j] = acc[0][j];
         }
 #pragma unroll
         for (int a = 0; a < W - 1; ++a)
 #pragma unroll
           for (int j = 0; j < UPL; ++j) acc[a][j] = acc[a + 1][j];
 #pragma unroll
-        for (int j = 0; j < UPL; ++j) acc[W - 1][j] = zero_unit<U>();
+        for (int j = 0; j < UPL; ++j) acc[W - 1][j] = zero_unit();
         ++i;
       }
     }
   }
 }
 
-// One launch over every bin of every wedge.  A pass covers chp = 32 UPL channels
-// (32 with paired units); the chunk size kc fills the shared-memory budget.
-template <int W, int UPL, bool PAIR>
+// One launch over every bin of every wedge.  A pass covers chp = 32 UPL channels;
+// the chunk size kc fills the shared-memory budget.
+template <int W, int UPL>
 cudaError_t launch_sweep(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s) {
   const long long NN = (long long)p->N * p->N;
   const int chp = 32 * UPL;
@@ -282,37 +253,35 @@ cudaError_t launch_sweep(const fio_plan_s *p, const void *g, void *grid, int B, 
   int kc = (int)std::min<size_t>(kSwMaxChunk, (kSwSmem - 64) / per) / 16 * 16;
   kc = std::max(kc, 16);
   const size_t smem = sw_meta_bytes(kc, W) + (size_t)kc * (chp + qpmax + nbmax) * 8;
-  cudaError_t e = cudaFuncSetAttribute(k_spread_sweep<W, UPL, PAIR>,
+  cudaError_t e = cudaFuncSetAttribute(k_spread_sweep<W, UPL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   if (p->n_bins1 > 0)
-    k_spread_sweep<W, UPL, PAIR><<<p->n_bins1, kSwThreads, smem, s>>>(
+    k_spread_sweep<W, UPL><<<p->n_bins1, kSwThreads, smem, s>>>(
         (const float2 *)g, (float2 *)grid, p->d_wedges, p->d_bins1, p->d_cstart,
         (const float2 *)p->d_alpha, p->d_warps, p->d_perm, NN, B, make_kbdev(p), p->horner, kc,
         chp, qpmax, nbmax, p->d_errword);
   return cudaGetLastError();
 }
 
-// Paired units with lane groups when a cell holds at most 32 channels, else
-// single-term units, UPL = ceil(channels / 32) of them per lane (up to the
-// register limit; more channels take several passes).
+// UPL = ceil(channels / 32) single-term units per lane (up to the register
+// limit; more channels take several passes).
 template <int W>
 cudaError_t sweep_w(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s) {
   int qpmax = 2;
   for (const WedgeDev &w : p->wedges) qpmax = std::max(qpmax, w.qp);
   const int nchmax = B * qpmax;
   if (nchmax >= (1 << 20)) return cudaErrorInvalidValue;  // the channel index divisions need < 2^20
-  if (nchmax <= 32) return launch_sweep<W, 1, true>(p, g, grid, B, s);
   constexpr int UM = max_upl(W);
   switch (std::min(UM, (nchmax + 31) / 32)) {
-    case 1: return launch_sweep<W, 1, false>(p, g, grid, B, s);
-    case 2: return launch_sweep<W, std::min(UM, 2), false>(p, g, grid, B, s);
-    case 3: return launch_sweep<W, std::min(UM, 3), false>(p, g, grid, B, s);
-    case 4: return launch_sweep<W, std::min(UM, 4), false>(p, g, grid, B, s);
-    case 5: return launch_sweep<W, std::min(UM, 5), false>(p, g, grid, B, s);
-    case 6: return launch_sweep<W, std::min(UM, 6), false>(p, g, grid, B, s);
-    case 7: return launch_sweep<W, std::min(UM, 7), false>(p, g, grid, B, s);
-    default: return launch_sweep<W, std::min(UM, 8), false>(p, g, grid, B, s);
+    case 1: return launch_sweep<W, 1>(p, g, grid, B, s);
+    case 2: return launch_sweep<W, std::min(UM, 2)>(p, g, grid, B, s);
+    case 3: return launch_sweep<W, std::min(UM, 3)>(p, g, grid, B, s);
+    case 4: return launch_sweep<W, std::min(UM, 4)>(p, g, grid, B, s);
+    case 5: return launch_sweep<W, std::min(UM, 5)>(p, g, grid, B, s);
+    case 6: return launch_sweep<W, std::min(UM, 6)>(p, g, grid, B, s);
+    case 7: return launch_sweep<W, std::min(UM, 7)>(p, g, grid, B, s);
+    default: return launch_sweep<W, std::min(UM, 8)>(p, g, grid, B, s);
   }
 }
 
