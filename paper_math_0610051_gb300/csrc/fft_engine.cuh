@@ -1,5 +1,5 @@
 // fft_engine.cuh -- batched 1D FFTs in shared memory (Stockham autosort,
-// mixed radix 2/3/4/5/8), used by every grid stage of the apply path.
+// mixed radix 2/3/4/5/8/9/16), used by every grid stage of the apply path.
 //
 // Data of `nl` lines of length n sit in shared memory element-major: element e
 // of line l is at buf[e * nl + l].  This is the natural layout of the NUFFT
@@ -147,12 +147,81 @@ template <typename C> __device__ __forceinline__ void bfly8(C *v, int sign) {
   }
 }
 
+// DFT_9 as 3 x 3: with r = 3 r1 + r2 and k = k1 + 3 k2,
+// V[k] = sum_r2 W3^(r2 k2) w9^(r2 k1) [sum_r1 v[3 r1 + r2] W3^(r1 k1)].
+template <typename C> __device__ __forceinline__ void bfly9(C *v, int sign) {
+  using T = decltype(v[0].x);
+  const T c1 = T(0.76604444311897803520), s1 = T(0.64278760968653932632);   // 2 pi / 9
+  const T c2 = T(0.17364817766693034885), s2 = T(0.98480775301220805936);   // 4 pi / 9
+  const T c4 = T(-0.93969262078590838405), s4 = T(0.34202014332566873304);  // 8 pi / 9
+  C a[3][3];
+#pragma unroll
+  for (int r2 = 0; r2 < 3; ++r2) {
+    a[r2][0] = v[r2];
+    a[r2][1] = v[3 + r2];
+    a[r2][2] = v[6 + r2];
+    bfly3(a[r2], sign);
+  }
+  const T sg = T(sign);
+  a[1][1] = cmul(a[1][1], C{c1, sg * s1});
+  a[1][2] = cmul(a[1][2], C{c2, sg * s2});
+  a[2][1] = cmul(a[2][1], C{c2, sg * s2});
+  a[2][2] = cmul(a[2][2], C{c4, sg * s4});
+#pragma unroll
+  for (int k1 = 0; k1 < 3; ++k1) {
+    C t[3] = {a[0][k1], a[1][k1], a[2][k1]};
+    bfly3(t, sign);
+    v[k1] = t[0];
+    v[k1 + 3] = t[1];
+    v[k1 + 6] = t[2];
+  }
+}
+
+// DFT_16 as 4 x 4: with r = 4 r1 + r2 and k = k1 + 4 k2,
+// V[k] = sum_r2 W4^(r2 k2) w16^(r2 k1) [sum_r1 v[4 r1 + r2] W4^(r1 k1)].
+template <typename C> __device__ __forceinline__ void bfly16(C *v, int sign) {
+  using T = decltype(v[0].x);
+  const T c1 = T(0.92387953251128675613), s1 = T(0.38268343236508977173);  // pi / 8
+  const T r2 = T(0.70710678118654752440);
+  const T sg = T(sign);
+  C a[4][4];
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    a[q][0] = v[q];
+    a[q][1] = v[4 + q];
+    a[q][2] = v[8 + q];
+    a[q][3] = v[12 + q];
+    bfly4(a[q], sign);
+  }
+  // w16^m for m = q k1: 1: (c1, s1), 2: (r2, r2), 3: (s1, c1), 4: i, 6: (-r2, r2), 9: (-c1, -s1)
+  a[1][1] = cmul(a[1][1], C{c1, sg * s1});
+  a[1][2] = cmul(a[1][2], C{r2, sg * r2});
+  a[1][3] = cmul(a[1][3], C{s1, sg * c1});
+  a[2][1] = cmul(a[2][1], C{r2, sg * r2});
+  a[2][2] = cmul_si(a[2][2], sign);
+  a[2][3] = cmul(a[2][3], C{-r2, sg * r2});
+  a[3][1] = cmul(a[3][1], C{s1, sg * c1});
+  a[3][2] = cmul(a[3][2], C{-r2, sg * r2});
+  a[3][3] = cmul(a[3][3], C{-c1, -sg * s1});
+#pragma unroll
+  for (int k1 = 0; k1 < 4; ++k1) {
+    C t[4] = {a[0][k1], a[1][k1], a[2][k1], a[3][k1]};
+    bfly4(t, sign);
+    v[k1] = t[0];
+    v[k1 + 4] = t[1];
+    v[k1 + 8] = t[2];
+    v[k1 + 12] = t[3];
+  }
+}
+
 template <int R, typename C> __device__ __forceinline__ void bfly(C *v, int sign) {
   if constexpr (R == 2) bfly2(v);
   if constexpr (R == 3) bfly3(v, sign);
   if constexpr (R == 4) bfly4(v, sign);
   if constexpr (R == 5) bfly5(v, sign);
   if constexpr (R == 8) bfly8(v, sign);
+  if constexpr (R == 9) bfly9(v, sign);
+  if constexpr (R == 16) bfly16(v, sign);
 }
 
 // One Stockham stage (decimation in time): for butterfly j of each line,
@@ -193,6 +262,8 @@ __device__ C *fft_exec(C *a, C *b, int n, int nl, const FftPlanDev &pl, int sign
   for (int s = 0; s < pl.nstages; ++s) {
     const int R = pl.radix[s];
     switch (R) {
+      case 16: fft_stage<16>(a, b, n, nl, Ns, sign, tw); break;
+      case 9: fft_stage<9>(a, b, n, nl, Ns, sign, tw); break;
       case 8: fft_stage<8>(a, b, n, nl, Ns, sign, tw); break;
       case 4: fft_stage<4>(a, b, n, nl, Ns, sign, tw); break;
       case 2: fft_stage<2>(a, b, n, nl, Ns, sign, tw); break;
@@ -221,14 +292,16 @@ __host__ __device__ inline FastDiv make_fastdiv(unsigned d) {
 __device__ __forceinline__ unsigned fdiv(unsigned x, const FastDiv &f) {
   return (unsigned)(((unsigned long long)x * f.M) >> 40);
 }
-// x / R for the radices 2, 3, 4, 5, 8 and x < 2^16 (multiply-shift constants
-// ceil(2^17 / 3) and ceil(2^18 / 5), exact on that range).
+// x / R for the radices 2, 3, 4, 5, 8, 9, 16 and x < 2^16 (multiply-shift
+// constants ceil(2^17 / 3), ceil(2^18 / 5) and ceil(2^19 / 9), exact on that range).
 __device__ __forceinline__ int div_radix(int x, int R) {
   switch (R) {
     case 2: return x >> 1;
     case 4: return x >> 2;
     case 8: return x >> 3;
+    case 16: return x >> 4;
     case 3: return (int)(((unsigned)x * 43691u) >> 17);
+    case 9: return (int)(((unsigned)x * 58255u) >> 19);
     default: return (int)(((unsigned)x * 52429u) >> 18);
   }
 }
@@ -300,6 +373,8 @@ __device__ void fft_exec_dif(C *a, int n, int nl, const FftPlanDev &pl, const C 
   for (int s = 0; s < pl.nstages; ++s) {
     const int R = pl.radix[s];
     switch (R) {
+      case 16: fft_stage_dif<16, SIGN>(a, n, nl, m, tw, lm); break;
+      case 9: fft_stage_dif<9, SIGN>(a, n, nl, m, tw, lm); break;
       case 8: fft_stage_dif<8, SIGN>(a, n, nl, m, tw, lm); break;
       case 4: fft_stage_dif<4, SIGN>(a, n, nl, m, tw, lm); break;
       case 2: fft_stage_dif<2, SIGN>(a, n, nl, m, tw, lm); break;

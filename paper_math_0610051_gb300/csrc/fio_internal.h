@@ -158,7 +158,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
 void free_plan_device(fio_plan_s *p);
 
 // Host helpers shared by plan.cpp and the launchers.
-std::vector<int> fft_factor(int n);   // radices (8, 4, 2, 3, 5), empty if n is not 2^a 3^b 5^c
+std::vector<int> fft_factor(int n);   // radices (16, 8, 4, 2, 9, 3, 5), empty if n is not 2^a 3^b 5^c
 int fft_good_size(int n);             // smallest even 2^a 3^b 5^c >= n
 
 // apply.cu launchers (return cudaGetLastError()).

@@ -44,9 +44,11 @@ constexpr int kValidationRows = 200;
 std::vector<int> fft_factor(int n) {
   std::vector<int> r;
   if (n < 2) return r;
+  while (n % 16 == 0) { r.push_back(16); n /= 16; }
   while (n % 8 == 0) { r.push_back(8); n /= 8; }
   while (n % 4 == 0) { r.push_back(4); n /= 4; }
   while (n % 2 == 0) { r.push_back(2); n /= 2; }
+  while (n % 9 == 0) { r.push_back(9); n /= 9; }
   while (n % 3 == 0) { r.push_back(3); n /= 3; }
   while (n % 5 == 0) { r.push_back(5); n /= 5; }
   if (n != 1) r.clear();
