@@ -24,15 +24,16 @@
 //
 // Candidates come in chunks in region order.  For each chunk the CTA forms the
 // KB weights and v for all channels once (alpha' and g are read once per
-// launch, whatever B is), then every warp sweeps.  A start row may continue in
-// the next chunk; the sweep state stays in registers.
+// launch, whatever B is), then every warp sweeps.  The copies of the next
+// chunk's alpha' rows and inputs are started before the sweep and land during
+// it (two staging buffers).  A start row may continue in the next chunk; the
+// sweep state stays in registers.
 //
 // A point whose window start disagrees with the bucket it was sorted into is
 // recorded in the plan's error word and skipped.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <type_traits>
 
 #include "apply_common.cuh"
 #include "bin_common.cuh"
@@ -45,7 +46,7 @@ namespace {
 constexpr unsigned kFull = 0xffffffffu;
 constexpr int kSwThreads = kBin * 32;  // one warp per cell column of a bin
 constexpr int kSwRegion = (kBin + kMaxKbWidth - 1) * (kBin + kMaxKbWidth - 1);
-constexpr int kSwSmem = 200 * 1024;    // dynamic shared memory budget
+constexpr int kSwSmem = 212 * 1024;    // dynamic shared memory budget
 constexpr int kSwMaxChunk = 512;
 
 // Registers: a lane keeps w x UPL accumulators of two floats; at most 30 of them.
@@ -53,9 +54,9 @@ __host__ __device__ constexpr int max_upl(int W) { return 30 / W < 1 ? 1 : (30 /
 
 __device__ __forceinline__ float2 zero_unit() { return make_float2(0.f, 0.f); }
 
-// Per-chunk shared arrays: weights [kc][2W] floats, sorted position and output
-// index [kc] ints, start column [kc] bytes, then v [kc][chp], the staged alpha'
-// rows [kc][qpmax] and the staged inputs g_b(x) [kc][nbmax] (complex values).
+// Per-candidate shared arrays of a chunk: weights [kc][2W] floats, sorted
+// position and output index [kc] ints, start column [kc] bytes; then the staged
+// alpha' rows [kc][qpmax] and inputs g_b(x) [kc][nbmax] (complex values).
 __host__ __device__ constexpr size_t sw_meta_bytes(int kc, int W) {
   return ((size_t)kc * (2 * W * 4 + 4 + 4 + 1) + 15) / 16 * 16;
 }
@@ -72,13 +73,12 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
   __shared__ int sRS[kSwRegion + 1];  // region-ordered first candidate of every start cell
   __shared__ int sGB[kSwRegion];      // sorted position of every start cell's first point
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  float(*sWt)[2 * W] = reinterpret_cast<float(*)[2 * W]>(smem_raw);
-  int *sPos = reinterpret_cast<int *>(smem_raw + (size_t)kc * 2 * W * 4);
-  int *sX = sPos + kc;
-  unsigned char *sCol = reinterpret_cast<unsigned char *>(sX + kc);
-  float2 *sV = reinterpret_cast<float2 *>(smem_raw + sw_meta_bytes(kc, W));
-  float2 *sA = sV + (size_t)kc * chp;    // alpha' rows of the chunk's candidates
-  float2 *sGi = sA + (size_t)kc * qpmax; // g_b(x) of the pass's inputs
+  // v of one chunk, then two buffers of the per-candidate data (weights, sorted
+  // position, output index, start column; staged alpha' rows and inputs): the
+  // next chunk is staged while this one is swept
+  float2 *sV = reinterpret_cast<float2 *>(smem_raw);
+  const size_t half = sw_meta_bytes(kc, W) + (size_t)kc * (qpmax + nbmax) * 8;
+  auto bufp = [&](int buf) { return smem_raw + (size_t)kc * chp * 8 + buf * half; };
 
   const int tid = threadIdx.x, lane = tid & 31, cl = tid >> 5;
   const int2 it = bins[blockIdx.x];  // (wedge, bin)
@@ -141,10 +141,18 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
 #pragma unroll
       for (int j = 0; j < UPL; ++j) acc[a][j] = zero_unit();
     int i = 0;  // next start row of the sweep
-    for (int ch = 0; ch < nchunks; ++ch) {
-      const int c = ch * kc;
+    // Chunk kk into buffer kk & 1: start cells by binary search, KB weights, and
+    // the copies of the candidates' alpha' rows and inputs, all in flight at once.
+    auto stage = [&](int kk) {
+      unsigned char *bp = bufp(kk & 1);
+      float(*sWt)[2 * W] = reinterpret_cast<float(*)[2 * W]>(bp);
+      int *sPos = reinterpret_cast<int *>(bp + (size_t)kc * 2 * W * 4);
+      int *sX = sPos + kc;
+      unsigned char *sCol = reinterpret_cast<unsigned char *>(sX + kc);
+      float2 *sA = reinterpret_cast<float2 *>(bp + sw_meta_bytes(kc, W));
+      float2 *sGi = sA + (size_t)kc * qpmax;
+      const int c = kk * kc;
       const int np = max(0, min(kc, total - c));
-      __syncthreads();  // the previous chunk is done with the chunk arrays
       for (int t = tid; t < np; t += kSwThreads) {
         const int idx = c + t;
         int lo = 0, hi = RC - 1;  // the start cell holding candidate idx
@@ -171,15 +179,27 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
         for (int bb = 0; bb < nbp; ++bb)
           cp_async<8>(sGi + t * nbmax + bb, gin + (long long)(b_lo + bb) * NN + x);
       }
+    };
+    __syncthreads();  // the previous pass is done with every buffer
+    stage(0);
+    for (int ch = 0; ch < nchunks; ++ch) {
+      const int c = ch * kc;
+      const int np = max(0, min(kc, total - c));
+      unsigned char *bp = bufp(ch & 1);
+      const float(*sWt)[2 * W] = reinterpret_cast<const float(*)[2 * W]>(bp);
+      const unsigned char *sCol = bp + (size_t)kc * 2 * W * 4 + 2 * (size_t)kc * 4;
+      const float2 *sA = reinterpret_cast<const float2 *>(bp + sw_meta_bytes(kc, W));
+      const float2 *sGi = sA + (size_t)kc * qpmax;
       cp_async_wait();
-      __syncthreads();
+      __syncthreads();  // chunk ch is staged; the sweep of chunk ch - 1 is done with v
       // v[t][c] = conj(alpha'_tr(x_t)) g_b(x_t) for the pass's channels ch0 + c = b qp + tr
       for (int e = tid; e < np * npc; e += kSwThreads) {
         const int t = (int)fdiv((unsigned)e, dnpc), cc = ch0 + e - t * npc;
         const int b = (int)fdiv((unsigned)cc, dqp), tr = cc - b * qp;
         sV[e] = cmulc(sGi[t * nbmax + b - b_lo], sA[t * qp + tr]);
       }
-      __syncthreads();
+      __syncthreads();  // v is complete
+      if (ch + 1 < nchunks) stage(ch + 1);  // lands while this chunk is swept
       if (cl >= H2) continue;
       const U *sVu = reinterpret_cast<const U *>(sV);
       // sweep the start rows this chunk reaches
@@ -249,10 +269,10 @@ cudaError_t launch_sweep(const fio_plan_s *p, const void *g, void *grid, int B, 
   int qpmax = 2;
   for (const WedgeDev &w : p->wedges) qpmax = std::max(qpmax, w.qp);
   const int nbmax = std::min(B, chp / 2 + 2);  // inputs one pass can touch (qp >= 2)
-  const size_t per = (size_t)2 * W * 4 + 4 + 4 + 1 + ((size_t)chp + qpmax + nbmax) * 8;
-  int kc = (int)std::min<size_t>(kSwMaxChunk, (kSwSmem - 64) / per) / 16 * 16;
+  const size_t per = 2 * ((size_t)2 * W * 4 + 4 + 4 + 1 + (size_t)(qpmax + nbmax) * 8) + (size_t)chp * 8;
+  int kc = (int)std::min<size_t>(kSwMaxChunk, (kSwSmem - 128) / per) / 16 * 16;
   kc = std::max(kc, 16);
-  const size_t smem = sw_meta_bytes(kc, W) + (size_t)kc * (chp + qpmax + nbmax) * 8;
+  const size_t smem = (size_t)kc * chp * 8 + 2 * (sw_meta_bytes(kc, W) + (size_t)kc * (qpmax + nbmax) * 8);
   cudaError_t e = cudaFuncSetAttribute(k_spread_sweep<W, UPL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
