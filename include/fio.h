@@ -98,6 +98,24 @@ typedef enum {
   FIO_FP64 = 1    /* complex128 everywhere */
 } fio_precision;
 
+/* Storage of the x-side factors gamma^x of the separated kernel (Sec. 3.2).
+ * FIO_ALPHA_STORED keeps gamma^x_t(x) for every x, wedge and rank term:
+ * L N^2 q complex values (4.7 GB at N = 1024, eps = 1e-4), read by every apply.
+ * FIO_ALPHA_RECOMPUTE keeps only what Eq. probnewfac needs to form them again,
+ * gamma^x = A_[C] V S^-1 (the sampled columns xi_c of each wedge and the r x q
+ * matrix V S^-1), plus per-x phase data, and forms gamma^x in every apply and
+ * adjoint, a few wedges at a time, into a buffer the plan owns.  The operator is
+ * the same to rounding: complex64 plans form the entries A_{x,xi_c} in single
+ * precision from cancellation-free forms of the residual phase, FP64 plans with
+ * the plan's own FP64 evaluation.  Not available for the Hankel amplitude on
+ * complex64 plans (FIO_EUNSUPPORTED): its demodulated Bessel functions need FP64.
+ * Complex64 recompute plans keep the plain warped points even when a surrogate
+ * is given (the single-precision forms assume the exact gradient as the warp). */
+typedef enum {
+  FIO_ALPHA_STORED = 0,
+  FIO_ALPHA_RECOMPUTE = 1
+} fio_alpha_mode;
+
 typedef struct {
   int precision;              /* fio_precision (default FIO_MIXED) */
   int L;                      /* number of wedges; 0 = ceil(sqrt(N)) rounded up to a multiple of 8 */
@@ -114,6 +132,9 @@ typedef struct {
                                  (Sec. 3.2 step 2); 0 = 0.25, at most 1 */
   double sep_target;          /* a sample is accepted when the validated separation error is
                                  at most sep_target * eps and q <= r/3; 0 = 0.5, at most 1 */
+  int alpha_mode;             /* fio_alpha_mode (default FIO_ALPHA_STORED) */
+  int alpha_group;            /* FIO_ALPHA_RECOMPUTE: wedges whose gamma^x is formed at a time
+                                 (the buffer holds that many wedges' factors); 0 = 4 */
 } fio_options;
 
 /* Fill *opt with the defaults listed above.  Returns FIO_EINVAL for NULL. */
@@ -144,6 +165,13 @@ fio_status fio_plan_create(int N, const fio_phase *phase, const fio_amplitude *a
  * call gives the same bits.  The order of the adjoint's spread sums depends on
  * the batch size, so one input may differ in its last bits between batch sizes. */
 fio_status fio_apply(fio_plan plan, const void *f, void *out, int batch, void *stream);
+
+/* out = L f for a real f (Eq. dft applied to f(x) + 0i): the same operator and
+ * result as fio_apply on the complex array with zero imaginary parts.
+ * f: device array of batch*N*N real values, float for FIO_MIXED plans and
+ * double for FIO_FP64, half the bytes of its complex form; out as for fio_apply
+ * (complex).  Same rules as fio_apply; out must not overlap f. */
+fio_status fio_apply_real(fio_plan plan, const void *f, void *out, int batch, void *stream);
 
 /* out = L* g (Sec. 3.5: gamma^x-conjugate multiply, type-1 NUFFT, conj(gamma^xi)
  * windowed gather, inverse FFT).  Same layout and rules as fio_apply.  The result
@@ -271,6 +299,10 @@ typedef struct {
   double sep_error;                 /* largest per-wedge estimate of the relative Frobenius
                                        error of the separated factors (Sec. 4, Table 1's
                                        estimator over every column, on 200 random rows) */
+  int alpha_mode;                   /* fio_alpha_mode of the plan */
+  int alpha_groups;                 /* recompute mode: regeneration groups per apply, else 0 */
+  unsigned long long bytes_recompute; /* recompute mode: sampled columns, V S^-1 and per-x phase
+                                       data (bytes_alpha is then the regeneration buffer) */
 } fio_plan_info;
 
 /* Plan summary (host struct filled). */

@@ -153,6 +153,24 @@ fio_status fio_apply(fio_plan p, const void *f, void *out, int batch, void *stre
   return e == cudaSuccess ? FIO_OK : cuda_fail(e, "fio_apply");
 }
 
+fio_status fio_apply_real(fio_plan p, const void *f, void *out, int batch, void *stream) {
+  if (!plan_ok(p)) return FIO_EINVAL;
+  if (!f || !out || batch < 1 || batch > p->max_batch) {
+    set_error("fio_apply_real: null pointers or batch outside [1, max_batch]");
+    return FIO_EINVAL;
+  }
+  // the real input spans half the bytes of the complex output: no overlap at all
+  const size_t rs = p->precision == FIO_FP64 ? 8 : 4;
+  const size_t n = (size_t)batch * p->N * p->N;
+  const char *fa = static_cast<const char *>(f), *oa = static_cast<const char *>(out);
+  if (fa < oa + 2 * rs * n && oa < fa + rs * n) {
+    set_error("fio_apply_real: out overlaps f");
+    return FIO_EINVAL;
+  }
+  cudaError_t e = launch_apply(p, f, out, batch, (cudaStream_t)stream, true);
+  return e == cudaSuccess ? FIO_OK : cuda_fail(e, "fio_apply_real");
+}
+
 fio_status fio_apply_adjoint(fio_plan p, const void *g, void *out, int batch, void *stream) {
   if (!plan_ok(p)) return FIO_EINVAL;
   if (!g || !out || g == out || batch < 1 || batch > p->max_batch) {
@@ -224,6 +242,9 @@ fio_status fio_plan_get_info(fio_plan p, fio_plan_info *info) {
   info->max_bin_points = p->max_bin_pts;
   info->mean_bin_points = p->mean_bin_pts;
   info->max_spread_candidates = p->max_cand;
+  info->alpha_mode = p->alpha_mode;
+  info->alpha_groups = p->alpha_mode == FIO_ALPHA_RECOMPUTE ? (int)p->grp_first.size() - 1 : 0;
+  info->bytes_recompute = (unsigned long long)rc_bytes(p);
   return FIO_OK;
 }
 

@@ -37,6 +37,9 @@ __host__ __device__ inline int fft_lines(int n, int prec) {
   return nl < 1 ? 1 : (nl > 32 ? 32 : nl);
 }
 constexpr int kFftThreads = 512;  // threads of the in-place line-FFT kernels
+// CTAs per SM of the column FFT: two for complex64 (64 registers a thread), so
+// that one CTA's loads and stores overlap the other's butterfly stages.
+template <typename T> constexpr int kFftCtas = sizeof(T) == 4 ? 2 : 1;
 template <typename T> __host__ __device__ constexpr int prec_of() {
   return sizeof(T) == 4 ? FIO_MIXED : FIO_FP64;
 }
@@ -44,9 +47,11 @@ template <typename T> __host__ __device__ constexpr int prec_of() {
 // --------------------------------------------------------------- S0 / S4d --
 // Unitary 2D DFT passes.  Rows: lines are rows of N contiguous elements.
 // load index (e + load_shift) mod N, store index (e + store_shift) mod N.
-template <typename T>
+// REAL: the input holds real values (T), read as x + 0i; the first pass of a
+// real f, which reads half the bytes of its complex form.
+template <typename T, bool REAL = false>
 __global__ void __launch_bounds__(kThreads)
-k_dft_rows(const Cx<T> *in, Cx<T> *out, int N, int nrows, int nl, int sign, int load_shift,
+k_dft_rows(const void *in_v, Cx<T> *out, int N, int nrows, int nl, int sign, int load_shift,
            int store_shift, FftPlanDev pl, const Cx<T> *tw_g) {
   using C = Cx<T>;
   extern __shared__ unsigned char smem_raw[];
@@ -65,11 +70,20 @@ k_dft_rows(const Cx<T> *in, Cx<T> *out, int N, int nrows, int nl, int sign, int 
       tw[k] = C{c, s};
     }
   }
-  for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
-    const int e = it % N, l = it / N;
-    cp_async_elem(&a[e * nlc + l], &in[(size_t)(r0 + l) * N + (e + load_shift) % N]);
+  if constexpr (REAL) {
+    const T *in = static_cast<const T *>(in_v);
+    for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
+      const int e = it % N, l = it / N;
+      a[e * nlc + l] = C{in[(size_t)(r0 + l) * N + (e + load_shift) % N], T(0)};
+    }
+  } else {
+    const C *in = static_cast<const C *>(in_v);
+    for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
+      const int e = it % N, l = it / N;
+      cp_async_elem(&a[e * nlc + l], &in[(size_t)(r0 + l) * N + (e + load_shift) % N]);
+    }
+    cp_async_wait();
   }
-  cp_async_wait();
   __syncthreads();
   C *res = fft_exec(a, b, N, nlc, pl, sign, tw);
   for (int it = threadIdx.x; it < N * nlc; it += blockDim.x) {
@@ -179,7 +193,7 @@ struct ColBlocks {
 };
 
 template <typename T>
-__global__ void __launch_bounds__(kFftThreads)
+__global__ void __launch_bounds__(kFftThreads, kFftCtas<T>)
 k_colfft(Cx<T> *__restrict__ grid, const WedgeDev *__restrict__ W,
          const FftPlanDev *__restrict__ ffts, const Cx<T> *__restrict__ tw_all,
          const ColBlocks cb, int B, int adjoint) {
@@ -318,29 +332,40 @@ static int pick_nl(int n, int precision, int want) {
   return nl;
 }
 
-template <typename K> static cudaError_t set_smem(K kernel, size_t bytes) {
-  if (bytes <= 48 * 1024) return cudaSuccess;
+// Dynamic shared memory above the 48 KB default.  max_shared: also ask for the
+// largest shared-memory carveout, so that two CTAs of the column FFT fit on an
+// SM (the row kernels gather through L1 and keep the default split).
+template <typename K> static cudaError_t set_smem(K kernel, size_t bytes, bool max_shared = false) {
+  cudaError_t e = cudaSuccess;
+  if (max_shared)
+    e = cudaFuncSetAttribute(kernel, cudaFuncAttributePreferredSharedMemoryCarveout,
+                             cudaSharedmemCarveoutMaxShared);
+  if (e != cudaSuccess || bytes <= 48 * 1024) return e;
   return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
 template <typename T>
 static cudaError_t dft2_impl(int N, const void *in, void *out, int batch, int inverse,
                              const FftPlanDev &pl, const void *d_tw, bool centred,
-                             cudaStream_t s) {
+                             cudaStream_t s, bool real_in = false) {
   using C = Cx<T>;
   const int prec = sizeof(T) == 8 ? FIO_FP64 : FIO_MIXED;
   const int nl = pick_nl(N, prec, 16);
   const size_t smem = apply_smem_bytes(N, nl, prec);
   cudaError_t e;
   if ((e = set_smem(k_dft_rows<T>, smem)) != cudaSuccess) return e;
+  if ((e = set_smem(k_dft_rows<T, true>, smem)) != cudaSuccess) return e;
   if ((e = set_smem(k_dft_cols<T>, smem)) != cudaSuccess) return e;
   const int sign = inverse ? +1 : -1;
   const int sh = centred ? N / 2 : 0;
   const int nrows = batch * N;
   // rows: forward stores shifted, inverse loads shifted
-  k_dft_rows<T><<<(nrows + nl - 1) / nl, kThreads, smem, s>>>(
-      (const C *)in, (C *)out, N, nrows, nl, sign, inverse ? sh : 0, inverse ? 0 : sh, pl,
-      (const C *)d_tw);
+  if (real_in)
+    k_dft_rows<T, true><<<(nrows + nl - 1) / nl, kThreads, smem, s>>>(
+        in, (C *)out, N, nrows, nl, sign, inverse ? sh : 0, inverse ? 0 : sh, pl, (const C *)d_tw);
+  else
+    k_dft_rows<T><<<(nrows + nl - 1) / nl, kThreads, smem, s>>>(
+        in, (C *)out, N, nrows, nl, sign, inverse ? sh : 0, inverse ? 0 : sh, pl, (const C *)d_tw);
   const int chunks = (N + nl - 1) / nl;
   k_dft_cols<T><<<batch * chunks, kThreads, smem, s>>>((const C *)out, (C *)out, N, nl, sign,
                                                       inverse ? sh : 0, inverse ? 0 : sh,
@@ -426,7 +451,8 @@ static FftPlanDev plan_for_N(const fio_plan_s *p, const void **tw) {
 
 template <typename T>
 static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int B,
-                              cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing) {
+                              cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing,
+                              bool real_in) {
   using C = Cx<T>;
   const int N = p->N, L = p->L;
   const void *twN;
@@ -435,7 +461,7 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
   // S0: fhat in natural order (no centring shift)
   {
     StageTimer st(p, s, FIO_STAGE_S0_DFT, timing);
-    e = dft2_impl<T>(N, f, fhat_ws, B, 0, plN, twN, false, s);
+    e = dft2_impl<T>(N, f, fhat_ws, B, 0, plN, twN, false, s, real_in);
     p->launches += 2;
   }
   if (e != cudaSuccess) return e;
@@ -451,19 +477,29 @@ static cudaError_t apply_impl(const fio_plan_s *p, const void *f, void *out, int
     p->launches += 1;
   }
   // S2
-  if ((e = set_smem(k_colfft<T>, g0.smem_col)) != cudaSuccess) return e;
+  if ((e = set_smem(k_colfft<T>, g0.smem_col, true)) != cudaSuccess) return e;
   {
     StageTimer st(p, s, FIO_STAGE_S2_COLFFT, timing);
     k_colfft<T><<<g0.col_blocks, kFftThreads, g0.smem_col, s>>>((C *)grid_ws, p->d_wedges, p->d_ffts,
                                                             (const C *)p->d_twiddle, g0.cb, B, 0);
     p->launches += 1;
   }
-  // S3
+  // S3 (recompute mode: gamma^x of a group of wedges is formed, then their
+  // points are interpolated, group after group; the stage time includes both)
   {
     StageTimer st(p, s, FIO_STAGE_S3_INTERP, timing);
-    e = launch_interp(p, grid_ws, out, B, s);
-    if (e != cudaSuccess) return e;
-    p->launches += 1;
+    if (p->alpha_mode == FIO_ALPHA_RECOMPUTE) {
+      for (int g = 0; g + 1 < (int)p->grp_first.size(); ++g) {
+        if ((e = regen_alpha(p, g, s)) != cudaSuccess) return e;
+        if ((e = launch_interp(p, grid_ws, out, B, s, group_range(p, g, g == 0))) != cudaSuccess)
+          return e;
+        p->launches += 2;
+      }
+    } else {
+      e = launch_interp(p, grid_ws, out, B, s, full_range(p));
+      if (e != cudaSuccess) return e;
+      p->launches += 1;
+    }
   }
   return cudaGetLastError();
 }
@@ -477,13 +513,22 @@ static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out,
   // S4a (writes every grid cell)
   {
     StageTimer st(p, s, FIO_STAGE_S4A_SPREAD);
-    e = launch_spread(p, gin, p->d_grid, B, s);
-    if (e != cudaSuccess) return e;
-    p->launches += 1;
+    if (p->alpha_mode == FIO_ALPHA_RECOMPUTE) {
+      for (int g = 0; g + 1 < (int)p->grp_first.size(); ++g) {
+        if ((e = regen_alpha(p, g, s)) != cudaSuccess) return e;
+        if ((e = launch_spread(p, gin, p->d_grid, B, s, group_range(p, g, false))) != cudaSuccess)
+          return e;
+        p->launches += 2;
+      }
+    } else {
+      e = launch_spread(p, gin, p->d_grid, B, s, full_range(p));
+      if (e != cudaSuccess) return e;
+      p->launches += 1;
+    }
   }
   // S4b columns
   const LaunchGeom g0 = geom(p, B);
-  if ((e = set_smem(k_colfft<T>, g0.smem_col)) != cudaSuccess) return e;
+  if ((e = set_smem(k_colfft<T>, g0.smem_col, true)) != cudaSuccess) return e;
   {
     StageTimer st(p, s, FIO_STAGE_S4B_COLFFT);
     k_colfft<T><<<g0.col_blocks, kFftThreads, g0.smem_col, s>>>((C *)p->d_grid, p->d_wedges,
@@ -516,15 +561,16 @@ static cudaError_t adjoint_impl(const fio_plan_s *p, const void *gin, void *out,
 }
 
 cudaError_t launch_apply(const fio_plan_s *p, const void *f, void *out, int batch,
-                         cudaStream_t s) {
-  return launch_apply_ws(p, f, out, batch, s, p->d_grid, p->d_fhat, true);
+                         cudaStream_t s, bool real_in) {
+  return launch_apply_ws(p, f, out, batch, s, p->d_grid, p->d_fhat, true, real_in);
 }
 
 cudaError_t launch_apply_ws(const fio_plan_s *p, const void *f, void *out, int batch,
-                            cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing) {
+                            cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing,
+                            bool real_in) {
   if (p->precision == FIO_FP64)
-    return apply_impl<double>(p, f, out, batch, s, grid_ws, fhat_ws, timing);
-  return apply_impl<float>(p, f, out, batch, s, grid_ws, fhat_ws, timing);
+    return apply_impl<double>(p, f, out, batch, s, grid_ws, fhat_ws, timing, real_in);
+  return apply_impl<float>(p, f, out, batch, s, grid_ws, fhat_ws, timing, real_in);
 }
 
 cudaError_t launch_adjoint(const fio_plan_s *p, const void *g, void *out, int batch,

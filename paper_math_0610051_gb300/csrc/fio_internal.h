@@ -16,6 +16,7 @@ constexpr int kMaxWedges = 256;  // largest L a plan accepts
 constexpr int kMaxFftLen = 4096;
 constexpr int kMaxKbWidth = 12;
 constexpr int kMaxHornerDeg = 15;
+constexpr int kTauMmax = 8;  // tau-mode phases: angular orders m in [-8, 8]
 
 // One FFT length: its radix factorisation (Stockham stages) and where its
 // twiddle table exp(-2 pi i k / n), k < n, starts in the plan's table.
@@ -46,6 +47,33 @@ struct WedgeDev {
   int tw1_off, tw2_off;   // twiddle offsets for m1 / m2 (copies of the FftPlanDev fields)
   int nb1, nb2;           // bins of kBin x kBin window-start cells per grid axis
   long long key_off;      // first entry of this wedge's bucket table (nb1 nb2 kBin^2 + 1 ints)
+  int rc_r;               // recompute mode: sampled columns of this wedge
+  long long rc_col_off;   // recompute mode: first RcCol of this wedge
+  long long rc_w_off;     // recompute mode: first entry of V S^-1 ([k][qp], complex)
+};
+
+// One sampled column xi_c of a wedge in the recompute storage mode: the values
+// the regeneration of gamma^x needs that do not depend on x, made in FP64 on
+// the host (rounded to float for complex64 plans).
+struct RcCol {
+  int k1, k2;      // the frequency xi_c
+  float ctk1;      // cos(theta_l) k1 (theta_l: the wedge's centre direction)
+  float stk2;      // sin(theta_l) k2
+  float cross2;    // (cos(theta_l) k2 - sin(theta_l) k1)^2
+  float fk1, fk2;  // k1, k2 as floats
+  float rsw;       // shift/wave phase: its residual, which does not depend on x
+  float ampc;      // the amplitude's column factor (1 + a2 cos theta), or 1
+  float pad[3];
+};
+
+// Phase and amplitude parameters on the device.
+struct PhaseDev {
+  int kind;          // FIO_PHASE_ELLIPSE_PRODUCT is carried as FIO_PHASE_ELLIPSE, ell_form = 1
+  int nmodes;
+  int ell_form;      // ellipse axes: 0 A + B sin sin / cos cos, 1 product form
+  double p[8];       // scalar parameters (shift/wave, ellipse)
+  int amp_kind;
+  double a1, a2;
 };
 
 // Points of a wedge are sorted by the grid cell where their KB window starts,
@@ -134,6 +162,26 @@ struct fio_plan_s {
   size_t bytes_total = 0;
   unsigned long long alg_bytes = 0;
 
+  // work lists per wedge: first item / bin pair / bin of wedge l (and the ends)
+  std::vector<int> item_off, bin_off, bin1_off;
+
+  // recompute storage mode (FIO_ALPHA_RECOMPUTE): d_alpha is the buffer of one
+  // group of wedges, d_wedges_rc the wedge table whose alpha_off is relative to
+  // the wedge's group
+  int alpha_mode = FIO_ALPHA_STORED;
+  std::vector<int> grp_first;           // first wedge of every group, then L
+  std::vector<int> rc_r;                // sampled columns per wedge
+  std::vector<long long> rc_col_off;    // first RcCol of wedge l
+  std::vector<long long> rc_w_off;      // first entry of wedge l's V S^-1 ([k][qp], complex)
+  long long rc_cols = 0, rc_w_elems = 0;
+  long long rc_x_elems = 0;             // bytes of d_rc_x
+  fio::WedgeDev *d_wedges_rc = nullptr;
+  fio::RcCol *d_rc_col = nullptr;
+  void *d_rc_w = nullptr;               // V S^-1 of every wedge, complex (plan precision)
+  void *d_rc_g = nullptr;               // tau phases, complex64 plans: G_{m,c} per column [c][kNm]
+  void *d_rc_x = nullptr;               // per-x phase data (complex64: floats; FP64: the plan's own)
+  fio::PhaseDev phase{};
+
   // diagnostics: launch counter and optional per-stage CUDA-event timing
   mutable unsigned long long launches = 0;
   bool timing = false;
@@ -144,6 +192,16 @@ struct fio_plan_s {
 };
 
 namespace fio {
+
+// Device bytes of the recompute mode's tables (columns, V S^-1, tau column
+// factors, per-x phase data, the second wedge table); 0 in the stored mode.
+inline size_t rc_bytes(const fio_plan_s *p) {
+  if (p->alpha_mode != FIO_ALPHA_RECOMPUTE) return 0;
+  const size_t cs = p->precision == FIO_FP64 ? 16 : 8;
+  return (size_t)p->rc_cols * sizeof(RcCol) + (size_t)p->rc_w_elems * cs +
+         (p->d_rc_g ? (size_t)p->rc_cols * (2 * kTauMmax + 1) * 8 : 0) + (size_t)p->rc_x_elems +
+         p->wedges.size() * sizeof(WedgeDev);
+}
 
 // Thread-local error text (api.cpp).
 void set_error(const std::string &msg);
@@ -156,20 +214,29 @@ fio_status load_plan(fio_plan_s *p, const char *path, int max_batch);
 fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_amplitude *amp,
                       double eps, const fio_options *opt);
 void free_plan_device(fio_plan_s *p);
+// Recompute mode: the wedge table whose alpha_off places each wedge's gamma^x
+// relative to its group (groups: wedges grp_first[g] .. grp_first[g + 1] - 1),
+// and the buffer size the largest group needs.
+std::vector<WedgeDev> rc_wedge_table(const std::vector<WedgeDev> &wedges,
+                                     const std::vector<int> &grp_first, long long NN,
+                                     long long *buf_elems);
 
 // Host helpers shared by plan.cpp and the launchers.
 std::vector<int> fft_factor(int n);   // radices (16, 8, 4, 2, 9, 3, 5), empty if n is not 2^a 3^b 5^c
 int fft_good_size(int n);             // smallest even 2^a 3^b 5^c >= n
 
 // apply.cu launchers (return cudaGetLastError()).
+// real_in: f holds B x N x N real values (float or double as the plan's
+// precision), read as x + 0i by the first DFT pass.
 cudaError_t launch_apply(const fio_plan_s *p, const void *f, void *out, int batch,
-                         cudaStream_t s);
+                         cudaStream_t s, bool real_in = false);
 cudaError_t launch_adjoint(const fio_plan_s *p, const void *g, void *out, int batch,
                            cudaStream_t s);
 // The forward apply on caller-chosen workspace: grid_ws holds grid_units * batch
 // complex values and fhat_ws N * N * batch; timing = false records no events.
 cudaError_t launch_apply_ws(const fio_plan_s *p, const void *f, void *out, int batch,
-                            cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing);
+                            cudaStream_t s, void *grid_ws, void *fhat_ws, bool timing,
+                            bool real_in = false);
 cudaError_t launch_dft2(int N, int precision, const void *in, void *out, int batch, int inverse,
                         const FftPlanDev *d_plan, const void *d_tw, cudaStream_t s);
 size_t apply_smem_bytes(int n, int nl, int precision);
@@ -184,25 +251,44 @@ cudaError_t sort_wedge_points(fio_plan_s *p, int l, std::vector<int> &cstart_hos
 // Work lists and bin statistics from every wedge's bucket table.
 cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> &cstart);
 void fit_horner(fio_plan_s *p);           // host: piecewise-polynomial KB weights
-cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B, cudaStream_t s);
-cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s);
-// interp_tasks.cu: the mixed-precision S3 (zeroes out, then accumulates).
+// The S3 / S4a work of one launch: the wedge table and the gamma^x array the
+// kernels read (a wedge's factors at alpha + alpha_off), and the sub-lists of
+// interpolation items, FP64 spread bin pairs and mixed-precision spread bins.
+// The stored mode runs every wedge in one launch; the recompute mode one group
+// of wedges per launch, right after their gamma^x is formed.
+struct WorkRange {
+  const WedgeDev *wedges;
+  const void *alpha;
+  const int4 *items;
+  int n_items;
+  const int2 *bins;
+  int n_bins;
+  const int2 *bins1;
+  int n_bins1;
+  bool clear;  // S3: zero the output before accumulating
+};
+WorkRange full_range(const fio_plan_s *p);
+WorkRange group_range(const fio_plan_s *p, int g, bool clear);
+cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B, cudaStream_t s,
+                          const WorkRange &wr);
+cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s,
+                          const WorkRange &wr);
+// interp_tasks.cu: the mixed-precision S3 (zeroes out if wr.clear, then accumulates).
 cudaError_t launch_interp_tasks(const fio_plan_s *p, const void *grid, void *out, int B,
-                                cudaStream_t s);
+                                cudaStream_t s, const WorkRange &wr);
 // spread.cu: the mixed-precision S4a, all inputs of a launch in one sweep.
 cudaError_t launch_spread_sweep(const fio_plan_s *p, const void *g, void *grid, int B,
-                                cudaStream_t s);
+                                cudaStream_t s, const WorkRange &wr);
+// alpha_regen.cu (recompute mode): gamma^x of group g's wedges into p->d_alpha,
+// in the layout of the stored mode with offsets from d_wedges_rc.
+cudaError_t regen_alpha(const fio_plan_s *p, int g, cudaStream_t s);
+// Per-x phase data of the complex64 regeneration from the plan's FP64 data:
+// ellipse (c1^2, c2^2) as float2 [x]; tau modes C_m(x) as float2 [x][2 kMmax + 1].
+cudaError_t rc_xdata_f32(const PhaseDev &ph, const void *d_xdata64, int N, void *d_out,
+                         cudaStream_t s);
 void release_timing_events(fio_plan_s *p);
 
 // plan_kernels.cu (FP64 plan construction on the device)
-struct PhaseDev {
-  int kind;          // FIO_PHASE_ELLIPSE_PRODUCT is carried as FIO_PHASE_ELLIPSE, ell_form = 1
-  int nmodes;
-  int ell_form;      // ellipse axes: 0 A + B sin sin / cos cos, 1 product form
-  double p[8];       // scalar parameters (shift/wave, ellipse)
-  int amp_kind;
-  double a1, a2;
-};
 
 cudaError_t plan_xdata(const PhaseDev &ph, const double *d_modes, int N, void *d_xdata,
                        cudaStream_t s);

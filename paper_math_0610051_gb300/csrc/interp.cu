@@ -444,7 +444,7 @@ int max_units(const fio_plan_s *p) {
 
 template <typename T, int W>
 cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, void *out, int B,
-                            bool spread, cudaStream_t s) {
+                            bool spread, cudaStream_t s, const WorkRange &wr) {
   using C = Cx<T>;
   const long long NN = (long long)p->N * p->N;
   const int numax = std::min(32, max_units<T>(p));
@@ -461,11 +461,13 @@ cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, voi
     e = cudaFuncSetAttribute(k_spread_bin<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    k_spread_bin<T, W><<<p->n_bins, threads, smem, s>>>(
-        (const C *)in, (C *)grid, p->d_wedges, p->d_bins, p->d_cstart, (const C *)p->d_alpha,
-        p->d_warps, p->d_perm, NN, B, make_kbdev(p), p->horner, chu, p->d_errword);
+    if (wr.n_bins > 0)
+      k_spread_bin<T, W><<<wr.n_bins, threads, smem, s>>>(
+          (const C *)in, (C *)grid, wr.wedges, wr.bins, p->d_cstart, (const C *)wr.alpha,
+          p->d_warps, p->d_perm, NN, B, make_kbdev(p), p->horner, chu, p->d_errword);
   } else {
-    e = cudaMemsetAsync(out, 0, sizeof(C) * (size_t)NN * B, s);
+    if (wr.clear) e = cudaMemsetAsync(out, 0, sizeof(C) * (size_t)NN * B, s);
+    else e = cudaSuccess;
     if (e != cudaSuccess) return e;
     const int cells = (kBin + W - 1) * (kBin + W - 1);
     const int chu = std::max(1, std::min(numax, kInterpSmemG / (16 * cells)));
@@ -474,9 +476,9 @@ cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, voi
     e = cudaFuncSetAttribute(k_interp_bin<T, W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
     if (e != cudaSuccess) return e;
-    if (p->n_items > 0)
-      k_interp_bin<T, W><<<p->n_items, 256, smem, s>>>(
-          (const C *)grid, p->d_wedges, p->d_items, (const C *)p->d_alpha, p->d_warps, p->d_perm,
+    if (wr.n_items > 0)
+      k_interp_bin<T, W><<<wr.n_items, 256, smem, s>>>(
+          (const C *)grid, wr.wedges, wr.items, (const C *)wr.alpha, p->d_warps, p->d_perm,
           (C *)out, NN, B, make_kbdev(p), p->horner, smem_g, p->d_errword);
   }
   return cudaGetLastError();
@@ -484,18 +486,18 @@ cudaError_t run_bin_kernels(const fio_plan_s *p, const void *in, void *grid, voi
 
 template <typename T>
 cudaError_t dispatch_w(const fio_plan_s *p, const void *in, void *grid, void *out, int B,
-                       bool spread, cudaStream_t s) {
+                       bool spread, cudaStream_t s, const WorkRange &wr) {
   switch (p->kb.w) {
-    case 3: return run_bin_kernels<T, 3>(p, in, grid, out, B, spread, s);
-    case 4: return run_bin_kernels<T, 4>(p, in, grid, out, B, spread, s);
-    case 5: return run_bin_kernels<T, 5>(p, in, grid, out, B, spread, s);
-    case 6: return run_bin_kernels<T, 6>(p, in, grid, out, B, spread, s);
-    case 7: return run_bin_kernels<T, 7>(p, in, grid, out, B, spread, s);
-    case 8: return run_bin_kernels<T, 8>(p, in, grid, out, B, spread, s);
-    case 9: return run_bin_kernels<T, 9>(p, in, grid, out, B, spread, s);
-    case 10: return run_bin_kernels<T, 10>(p, in, grid, out, B, spread, s);
-    case 11: return run_bin_kernels<T, 11>(p, in, grid, out, B, spread, s);
-    case 12: return run_bin_kernels<T, 12>(p, in, grid, out, B, spread, s);
+    case 3: return run_bin_kernels<T, 3>(p, in, grid, out, B, spread, s, wr);
+    case 4: return run_bin_kernels<T, 4>(p, in, grid, out, B, spread, s, wr);
+    case 5: return run_bin_kernels<T, 5>(p, in, grid, out, B, spread, s, wr);
+    case 6: return run_bin_kernels<T, 6>(p, in, grid, out, B, spread, s, wr);
+    case 7: return run_bin_kernels<T, 7>(p, in, grid, out, B, spread, s, wr);
+    case 8: return run_bin_kernels<T, 8>(p, in, grid, out, B, spread, s, wr);
+    case 9: return run_bin_kernels<T, 9>(p, in, grid, out, B, spread, s, wr);
+    case 10: return run_bin_kernels<T, 10>(p, in, grid, out, B, spread, s, wr);
+    case 11: return run_bin_kernels<T, 11>(p, in, grid, out, B, spread, s, wr);
+    case 12: return run_bin_kernels<T, 12>(p, in, grid, out, B, spread, s, wr);
   }
   return cudaErrorNotSupported;
 }
@@ -539,9 +541,15 @@ cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> 
   long long nonempty = 0, total = 0;
   int maxb = 0;
   long long maxc = 0;
+  p->item_off.assign(p->L + 1, 0);
+  p->bin_off.assign(p->L + 1, 0);
+  p->bin1_off.assign(p->L + 1, 0);
   for (int l = 0; l < p->L; ++l) {
     const WedgeDev &w = p->wedges[l];
     const std::vector<int> &cs = cstart[l];
+    p->item_off[l] = (int)items.size();
+    p->bin_off[l] = (int)bins.size();
+    p->bin1_off[l] = (int)bins1.size();
     for (int bin = 0; bin < w.nb1 * w.nb2; ++bin) {
       const int beg = cs[(size_t)bin * kBin * kBin], end = cs[(size_t)(bin + 1) * kBin * kBin];
       const int ipts = item_points(W);
@@ -570,6 +578,9 @@ cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> 
   p->n_items = (int)items.size();
   p->n_bins = (int)bins.size();
   p->n_bins1 = (int)bins1.size();
+  p->item_off[p->L] = p->n_items;
+  p->bin_off[p->L] = p->n_bins;
+  p->bin1_off[p->L] = p->n_bins1;
   p->max_bin_pts = maxb;
   p->mean_bin_pts = nonempty ? (double)total / nonempty : 0.0;
   p->max_cand = (int)maxc;
@@ -587,21 +598,36 @@ cudaError_t build_work_lists(fio_plan_s *p, const std::vector<std::vector<int>> 
   return cudaMemcpy(p->d_bins, bins.data(), sizeof(int2) * bins.size(), cudaMemcpyHostToDevice);
 }
 
-cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B,
-                          cudaStream_t s) {
-  if (p->precision == FIO_FP64) return dispatch_w<double>(p, nullptr, (void *)grid, out, B, false, s);
-  return launch_interp_tasks(p, grid, out, B, s);
+WorkRange full_range(const fio_plan_s *p) {
+  return WorkRange{p->d_wedges, p->d_alpha, p->d_items, p->n_items, p->d_bins, p->n_bins,
+                   p->d_bins1, p->n_bins1, true};
 }
 
-cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s) {
-  if (p->precision == FIO_FP64) return dispatch_w<double>(p, g, grid, nullptr, B, true, s);
+WorkRange group_range(const fio_plan_s *p, int g, bool clear) {
+  const int l0 = p->grp_first[g], l1 = p->grp_first[g + 1];
+  const int i0 = p->item_off[l0], b0 = p->bin_off[l0], c0 = p->bin1_off[l0];
+  return WorkRange{p->d_wedges_rc, p->d_alpha, p->d_items + i0, p->item_off[l1] - i0,
+                   p->d_bins + b0, p->bin_off[l1] - b0, p->d_bins1 + c0, p->bin1_off[l1] - c0,
+                   clear};
+}
+
+cudaError_t launch_interp(const fio_plan_s *p, const void *grid, void *out, int B,
+                          cudaStream_t s, const WorkRange &wr) {
+  if (p->precision == FIO_FP64)
+    return dispatch_w<double>(p, nullptr, (void *)grid, out, B, false, s, wr);
+  return launch_interp_tasks(p, grid, out, B, s, wr);
+}
+
+cudaError_t launch_spread(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s,
+                          const WorkRange &wr) {
+  if (p->precision == FIO_FP64) return dispatch_w<double>(p, g, grid, nullptr, B, true, s, wr);
   // one lane per channel pays when a cell holds more than 32 channels (several
   // inputs); a single input takes the bin-pair kernel, whose lane groups own a
   // column each
   int qpmax = 2;
   for (const WedgeDev &w : p->wedges) qpmax = std::max(qpmax, w.qp);
-  if (B * qpmax <= 32) return dispatch_w<float>(p, g, grid, nullptr, B, true, s);
-  return launch_spread_sweep(p, g, grid, B, s);
+  if (B * qpmax <= 32) return dispatch_w<float>(p, g, grid, nullptr, B, true, s, wr);
+  return launch_spread_sweep(p, g, grid, B, s, wr);
 }
 
 }  // namespace fio

@@ -91,13 +91,14 @@ __device__ __forceinline__ void stage_footprint(float4 *sG, const float2 *gw, in
                                                 int fh, int fw, int m1, int m2, int nch,
                                                 int cbase, int nuc) {
   const int wid = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarp = blockDim.x >> 5;
+  const FastDiv dnuc = make_fastdiv((unsigned)nuc);
   for (int f1 = wid; f1 < fh; f1 += nwarp) {
     int g1 = r0 + f1;
     if (g1 >= m1) g1 -= m1;
     const float2 *rowsrc = gw + (long long)g1 * m2 * nch + cbase;
     float4 *rowdst = sG + f1 * fw * nuc;
     for (int e = lane; e < fw * nuc; e += 32) {
-      const int f2 = e / nuc, k = e - f2 * nuc;
+      const int f2 = (int)fdiv((unsigned)e, dnuc), k = e - f2 * nuc;
       int g2 = c0 + f2;
       if (g2 >= m2) g2 -= m2;
       cp_async<16>(&rowdst[e], reinterpret_cast<const float4 *>(rowsrc + (long long)g2 * nch) + k);
@@ -270,26 +271,28 @@ k_interp_tasks(const float2 *__restrict__ grid, const WedgeDev *__restrict__ Wd,
 // points, so that one CTA's staging overlaps the other's arithmetic; several
 // stages run one CTA of 512 threads per SM with two buffers.
 template <int W>
-cudaError_t launch_w(const fio_plan_s *p, const void *grid, void *out, int B, cudaStream_t s) {
+cudaError_t launch_w(const fio_plan_s *p, const void *grid, void *out, int B, cudaStream_t s,
+                     const WorkRange &wr) {
   const long long NN = (long long)p->N * p->N;
   constexpr int FC = (kBin + W - 1) * (kBin + W - 1);
   int numax = 1;
   for (const WedgeDev &w : p->wedges) numax = std::max(numax, w.qp / 2);
   const bool single = B == 1 && (size_t)FC * numax * 16 + it_item_bytes(512, W) <= kItSmem / 2;
   const int cap = single ? std::min(512, item_points(W)) : item_points(W);
-  const int nbuf = single ? 1 : 2, threads = single ? 256 : 512;
+  const int nbuf = single ? 1 : 2, threads = single ? 256 : kItThreads;
   const size_t budget = single ? kItSmem / 2 : kItSmem;
   const size_t item = it_item_bytes(cap, W);
   const int chu = (int)std::min<size_t>(std::min(numax, 32), (budget - item) / (nbuf * (size_t)FC * 16));
   if (chu < 1) return cudaErrorInvalidConfiguration;
   const size_t smem = item + nbuf * (size_t)FC * chu * 16;
-  cudaError_t e = cudaMemsetAsync(out, 0, sizeof(float2) * (size_t)NN * B, s);
+  cudaError_t e = cudaSuccess;
+  if (wr.clear) e = cudaMemsetAsync(out, 0, sizeof(float2) * (size_t)NN * B, s);
   if (e != cudaSuccess) return e;
   e = cudaFuncSetAttribute(k_interp_tasks<W>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (p->n_items > 0)
-    k_interp_tasks<W><<<p->n_items, threads, smem, s>>>(
-        (const float2 *)grid, p->d_wedges, p->d_items, (const float2 *)p->d_alpha, p->d_warps,
+  if (wr.n_items > 0)
+    k_interp_tasks<W><<<wr.n_items, threads, smem, s>>>(
+        (const float2 *)grid, wr.wedges, wr.items, (const float2 *)wr.alpha, p->d_warps,
         p->d_perm, (float2 *)out, NN, B, make_kbdev(p), p->horner, cap, chu, nbuf, p->d_errword);
   return cudaGetLastError();
 }
@@ -297,18 +300,18 @@ cudaError_t launch_w(const fio_plan_s *p, const void *grid, void *out, int B, cu
 }  // namespace
 
 cudaError_t launch_interp_tasks(const fio_plan_s *p, const void *grid, void *out, int B,
-                                cudaStream_t s) {
+                                cudaStream_t s, const WorkRange &wr) {
   switch (p->kb.w) {
-    case 3: return launch_w<3>(p, grid, out, B, s);
-    case 4: return launch_w<4>(p, grid, out, B, s);
-    case 5: return launch_w<5>(p, grid, out, B, s);
-    case 6: return launch_w<6>(p, grid, out, B, s);
-    case 7: return launch_w<7>(p, grid, out, B, s);
-    case 8: return launch_w<8>(p, grid, out, B, s);
-    case 9: return launch_w<9>(p, grid, out, B, s);
-    case 10: return launch_w<10>(p, grid, out, B, s);
-    case 11: return launch_w<11>(p, grid, out, B, s);
-    case 12: return launch_w<12>(p, grid, out, B, s);
+    case 3: return launch_w<3>(p, grid, out, B, s, wr);
+    case 4: return launch_w<4>(p, grid, out, B, s, wr);
+    case 5: return launch_w<5>(p, grid, out, B, s, wr);
+    case 6: return launch_w<6>(p, grid, out, B, s, wr);
+    case 7: return launch_w<7>(p, grid, out, B, s, wr);
+    case 8: return launch_w<8>(p, grid, out, B, s, wr);
+    case 9: return launch_w<9>(p, grid, out, B, s, wr);
+    case 10: return launch_w<10>(p, grid, out, B, s, wr);
+    case 11: return launch_w<11>(p, grid, out, B, s, wr);
+    case 12: return launch_w<12>(p, grid, out, B, s, wr);
   }
   return cudaErrorNotSupported;
 }

@@ -570,11 +570,28 @@ fio_status cuda_status(cudaError_t e, const char *what) {
     if (st_ != FIO_OK) return st_;                          \
   } while (0)
 
+std::vector<WedgeDev> rc_wedge_table(const std::vector<WedgeDev> &wedges,
+                                     const std::vector<int> &grp_first, long long NN,
+                                     long long *buf_elems) {
+  std::vector<WedgeDev> wrc = wedges;
+  long long most = 0;
+  for (size_t g = 0; g + 1 < grp_first.size(); ++g) {
+    long long rel = 0;
+    for (int l = grp_first[g]; l < grp_first[g + 1]; ++l) {
+      wrc[l].alpha_off = rel;
+      rel += (long long)wrc[l].qp * NN;
+    }
+    most = std::max(most, rel);
+  }
+  *buf_elems = most;
+  return wrc;
+}
+
 void free_plan_device(fio_plan_s *p) {
   void *ptrs[] = {p->d_wedges, p->d_rows,  p->d_ffts,    p->d_twiddle, p->d_alpha,
                   p->d_beta,   p->d_warp,  p->d_grid,    p->d_fhat,    p->d_errword,
                   p->d_warps,  p->d_perm,  p->d_cstart,  p->d_items,   p->d_bins,
-                  p->d_bins1};
+                  p->d_bins1,  p->d_wedges_rc, p->d_rc_col, p->d_rc_w, p->d_rc_g, p->d_rc_x};
   for (void *q : ptrs)
     if (q) cudaFree(q);
   p->d_wedges = nullptr; p->d_rows = nullptr; p->d_ffts = nullptr; p->d_twiddle = nullptr;
@@ -583,6 +600,8 @@ void free_plan_device(fio_plan_s *p) {
   p->d_warps = nullptr; p->d_perm = nullptr; p->d_cstart = nullptr; p->d_items = nullptr;
   p->d_bins = nullptr;
   p->d_bins1 = nullptr;
+  p->d_wedges_rc = nullptr; p->d_rc_col = nullptr; p->d_rc_w = nullptr; p->d_rc_g = nullptr;
+  p->d_rc_x = nullptr;
 }
 
 // Piecewise polynomials of the KB kernel on the w unit intervals of a window:
@@ -706,9 +725,20 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     set_error("sep_cut and sep_target must lie in [0, 1] (0 = default)");
     return FIO_EINVAL;
   }
+  if ((opt.alpha_mode != FIO_ALPHA_STORED && opt.alpha_mode != FIO_ALPHA_RECOMPUTE) ||
+      opt.alpha_group < 0) {
+    set_error("alpha_mode must be FIO_ALPHA_STORED or FIO_ALPHA_RECOMPUTE, alpha_group >= 0");
+    return FIO_EINVAL;
+  }
+  const bool recompute = opt.alpha_mode == FIO_ALPHA_RECOMPUTE;
+  if (recompute && opt.precision == FIO_MIXED && amp1.kind == FIO_AMP_HANKEL) {
+    set_error("FIO_ALPHA_RECOMPUTE with the Hankel amplitude needs an FP64 plan");
+    return FIO_EUNSUPPORTED;
+  }
 
   p->N = N; p->L = L; p->eps = eps; p->sigma = sigma; p->precision = opt.precision;
   p->max_batch = max_batch;
+  p->alpha_mode = opt.alpha_mode;
   p->kb.w = w;
   p->kb.beta = kb_beta_for(w, sigma);
   cudaGetDevice(&p->device);
@@ -790,6 +820,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   ph.amp_kind = amp1.kind;
   ph.a1 = amp1.a1;
   ph.a2 = amp1.a2;
+  p->phase = ph;
   double *d_modes = nullptr;
   {
     const int nprm = ph.nmodes ? 5 * ph.nmodes : nscal;
@@ -820,7 +851,10 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     p->sur_warp_cycles = xi_max * (si->heldout_tau_maxerr + si->heldout_dtheta_maxerr);
     p->sur_residual_cycles = xi_max * si->heldout_tau_maxerr;
     const double budget = opt.surrogate_warp_budget > 0 ? opt.surrogate_warp_budget : 0.5;
-    if (p->sur_warp_cycles <= budget) {
+    // the single-precision regeneration of the recompute mode writes the residual
+    // phase with the exact gradient as the warp, so it keeps the plain warp
+    const bool rc32 = recompute && p->precision == FIO_MIXED;
+    if (p->sur_warp_cycles <= budget && !rc32) {
       FIO_CK(surrogate_warp(opt.surrogate, N, L, p->d_wedges, p->d_warp), "surrogate warp");
       p->sur_warp = 1;
     }
@@ -1100,8 +1134,15 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
 
   // ---- layout of the factors and grids
   long long aoff = 0, boff = 0, gunit = 0, koff = 0;
-  for (auto &wd : p->wedges) {
+  long long rc_cols = 0, rc_wn = 0;
+  for (int l = 0; l < L; ++l) {
+    WedgeDev &wd = p->wedges[l];
     wd.qp = wd.q + (wd.q & 1);
+    wd.rc_r = recompute ? (int)sep[l].C.size() : 0;
+    wd.rc_col_off = rc_cols;
+    wd.rc_w_off = rc_wn;
+    rc_cols += wd.rc_r;
+    rc_wn += (long long)wd.rc_r * wd.qp;
     wd.alpha_off = aoff;
     wd.beta_off = boff;
     wd.grid_unit = gunit;
@@ -1114,11 +1155,26 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     koff += (long long)wd.nb1 * wd.nb2 * kBin * kBin + 1;
   }
   p->alpha_elems = aoff;
+  // recompute mode: gamma^x of alpha_group wedges at a time, in a buffer the
+  // size of the largest group; the wedge table d_wedges_rc places each wedge's
+  // factors relative to its group
+  std::vector<WedgeDev> wrc;
+  long long abuf = aoff;
+  if (recompute) {
+    const int G = opt.alpha_group > 0 ? std::min(opt.alpha_group, L) : std::min(4, L);
+    p->grp_first.clear();
+    for (int l = 0; l < L; l += G) p->grp_first.push_back(l);
+    p->grp_first.push_back(L);
+    wrc = rc_wedge_table(p->wedges, p->grp_first, NN, &abuf);
+    p->rc_cols = rc_cols;
+    p->rc_w_elems = rc_wn;
+    p->alpha_elems = abuf;
+  }
   p->cstart_elems = koff;
   p->twiddle_elems = (long long)tw.size() / 2;
   p->beta_elems = boff;
   p->grid_units = gunit;
-  FIO_CK(dev_alloc(&p->d_alpha, (size_t)aoff * cs), "alloc alpha");
+  FIO_CK(dev_alloc(&p->d_alpha, (size_t)abuf * cs), "alloc alpha");
   FIO_CK(dev_alloc(&p->d_beta, (size_t)boff * cs), "alloc beta");
   FIO_CK(dev_alloc(&p->d_grid, (size_t)gunit * max_batch * cs), "alloc grids");
   FIO_CK(dev_alloc(&p->d_fhat, (size_t)NN * max_batch * cs), "alloc spectrum");
@@ -1128,7 +1184,7 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   FIO_CK(dev_alloc((void **)&p->d_errword, sizeof(int)), "alloc error word");
   FIO_CK(cudaMemset(p->d_errword, 0, sizeof(int)), "clear error word");
   // the padded rank term (t = q when q is odd) must stay exactly zero
-  FIO_CK(cudaMemset(p->d_alpha, 0, (size_t)aoff * cs), "clear alpha");
+  FIO_CK(cudaMemset(p->d_alpha, 0, (size_t)abuf * cs), "clear alpha");
   FIO_CK(cudaMemset(p->d_beta, 0, (size_t)boff * cs), "clear beta");
   FIO_CK(cudaMemcpy(p->d_wedges, p->wedges.data(), sizeof(WedgeDev) * L, cudaMemcpyHostToDevice), "upload wedges");
   {
@@ -1155,18 +1211,55 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
     if (s != FIO_OK) return s;
   }
   std::vector<std::vector<int>> cstart(L);
+  // recompute mode: the x-independent values of every sampled column, and V S^-1
+  std::vector<RcCol> rc_col;
+  std::vector<cd> rc_w;
+  std::vector<float> rc_g;
+  const bool tau_g = recompute && ph.kind == FIO_PHASE_TAU_MODES && p->precision == FIO_MIXED;
   for (int l = 0; l < L; ++l) {
     const WedgeDev &wd = p->wedges[l];
     const Sep &sp = sep[l];
     const int rc = (int)sp.C.size(), q = sp.q, nr = (int)sp.R.size();
     FIO_CK(sort_wedge_points(p, l, cstart[l]), "point sort");
-    fio_status s = eval_cols(l, sp.C);
-    if (s != FIO_OK) return s;
-    FIO_CK(cudaMemcpy(d_W, sp.W.data(), sizeof(cd) * rc * q, cudaMemcpyHostToDevice), "upload W");
-    FIO_CK(plan_form_alpha(d_AC, N, rc, q, d_W, wd, p->d_warp + (size_t)l * NN,
-                           p->d_perm + (size_t)l * NN,
-                           (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision, 0),
-           "alpha kernel");
+    if (recompute) {
+      const double th = 2.0 * M_PI * l / L, ct = std::cos(th), st = std::sin(th);
+      for (int k = 0; k < rc; ++k) {
+        const int k1 = pk1[wd.pt_off + sp.C[k]], k2 = pk2[wd.pt_off + sp.C[k]];
+        const double r = std::hypot((double)k1, (double)k2);
+        const double dot = ct * k1 + st * k2, cross = ct * k2 - st * k1;
+        RcCol c{};
+        c.k1 = k1;
+        c.k2 = k2;
+        c.ctk1 = (float)(ct * k1);
+        c.stk2 = (float)(st * k2);
+        c.cross2 = (float)(cross * cross);
+        c.fk1 = (float)k1;
+        c.fk2 = (float)k2;
+        c.rsw = (ph.kind == FIO_PHASE_SHIFT_WAVE && r > 0) ? (float)(ph.p[2] * cross * cross / (r + dot)) : 0.f;
+        c.ampc = ph.amp_kind == FIO_AMP_SEPARABLE ? (float)(1.0 + ph.a2 * (r > 0 ? k1 / r : 1.0)) : 1.f;
+        rc_col.push_back(c);
+        for (int t = 0; t < wd.qp; ++t) rc_w.push_back(t < q ? sp.W[(size_t)k * q + t] : cd(0.0));
+        if (tau_g) {
+          // G_m = |xi| e^{i m theta_l} ((cos m d - cos d) + i (sin m d - m sin d))
+          const double d = r > 0 ? std::atan2(cross, dot) : 0.0;
+          for (int m = -kTauMmax; m <= kTauMmax; ++m) {
+            const double re = -2.0 * std::sin((m + 1) * d / 2) * std::sin((m - 1) * d / 2);
+            const double im = std::sin(m * d) - m * std::sin(d);
+            const cd gm = r * std::polar(1.0, m * th) * cd(re, im);
+            rc_g.push_back((float)gm.real());
+            rc_g.push_back((float)gm.imag());
+          }
+        }
+      }
+    } else {
+      fio_status s = eval_cols(l, sp.C);
+      if (s != FIO_OK) return s;
+      FIO_CK(cudaMemcpy(d_W, sp.W.data(), sizeof(cd) * rc * q, cudaMemcpyHostToDevice), "upload W");
+      FIO_CK(plan_form_alpha(d_AC, N, rc, q, d_W, wd, p->d_warp + (size_t)l * NN,
+                             p->d_perm + (size_t)l * NN,
+                             (char *)p->d_alpha + (size_t)wd.alpha_off * cs, p->precision, 0),
+             "alpha kernel");
+    }
     std::vector<double> dec(wd.npts);
     for (int i = 0; i < wd.npts; ++i)
       dec[i] = 1.0 / (kb_phihat_host((double)x1p[l][i] / wd.m1, w, p->kb.beta) *
@@ -1198,6 +1291,38 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
                           d_pk2, d_dec, beta_l, p->precision, 0),
            "beta kernel");
   }
+  if (recompute) {
+    fio_status s = upload((void **)&p->d_rc_col, rc_col, "upload sampled columns");
+    if (s != FIO_OK) return s;
+    if (p->precision == FIO_FP64) {
+      s = upload(&p->d_rc_w, rc_w, "upload V S^-1");
+    } else {
+      std::vector<float> wf(2 * rc_w.size());
+      for (size_t e = 0; e < rc_w.size(); ++e) {
+        wf[2 * e] = (float)rc_w[e].real();
+        wf[2 * e + 1] = (float)rc_w[e].imag();
+      }
+      s = upload(&p->d_rc_w, wf, "upload V S^-1");
+    }
+    if (s != FIO_OK) return s;
+    if (tau_g) {
+      s = upload(&p->d_rc_g, rc_g, "upload tau column factors");
+      if (s != FIO_OK) return s;
+    }
+    s = upload((void **)&p->d_wedges_rc, wrc, "upload wedge table");
+    if (s != FIO_OK) return s;
+    // per-x phase data: the plan's own for FP64 plans, single precision otherwise
+    const bool xdep = ph.kind == FIO_PHASE_ELLIPSE || ph.kind == FIO_PHASE_TAU_MODES;
+    if (p->precision == FIO_FP64) {
+      tmp.ptrs.erase(std::find(tmp.ptrs.begin(), tmp.ptrs.end(), d_xdata));
+      p->d_rc_x = d_xdata;
+      p->rc_x_elems = (long long)plan_xdata_bytes(ph, N);
+    } else if (xdep) {
+      p->rc_x_elems = (long long)plan_xdata_bytes(ph, N) / 2;  // bytes: float2 for double2
+      FIO_CK(dev_alloc(&p->d_rc_x, (size_t)p->rc_x_elems), "alloc phase data");
+      FIO_CK(rc_xdata_f32(ph, d_xdata, N, p->d_rc_x, 0), "phase data");
+    }
+  }
   FIO_CK(cudaDeviceSynchronize(), "plan construction");
   FIO_CK(build_work_lists(p, cstart), "work lists");
 
@@ -1215,8 +1340,8 @@ fio_status build_plan(fio_plan_s *p, int N, const fio_phase *phase, const fio_am
   for (double e : p->wedge_err) p->sep_err = std::max(p->sep_err, e);
   p->bytes_total = (sizeof(uint2) + sizeof(uint32_t)) * (size_t)L * NN + sizeof(int) * (size_t)koff +
                    sizeof(int4) * (size_t)p->n_items +
-                   sizeof(int2) * (size_t)(p->n_bins + p->n_bins1) +
-                   (size_t)(aoff + boff) * cs + (size_t)gunit * max_batch * cs +
+                   sizeof(int2) * (size_t)(p->n_bins + p->n_bins1) + rc_bytes(p) +
+                   (size_t)(abuf + boff) * cs + (size_t)gunit * max_batch * cs +
                    (size_t)NN * max_batch * cs + (size_t)NN * L * sizeof(uint2) +
                    tw.size() / 2 * cs + p->rows.size() * sizeof(RowDev) +
                    p->wedges.size() * sizeof(WedgeDev) + p->ffts.size() * sizeof(FftPlanDev);

@@ -10,7 +10,10 @@
 // wedge frequencies, the KB polynomials) and the device arrays, copied as they
 // are (twiddles, factors alpha' and beta', warped points in plan and sorted
 // order, point order, bucket tables, work lists).  The NUFFT grid and spectrum
-// workspace is not stored: load allocates it for the requested batch.
+// workspace is not stored: load allocates it for the requested batch.  A plan
+// in the recompute storage mode stores, in place of gamma^x, its phase
+// parameters, the sampled columns, V S^-1 and the per-x phase data; its
+// regeneration buffer is allocated on load.
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -26,7 +29,7 @@ namespace fio {
 namespace {
 
 constexpr char kMagic[8] = {'F', 'I', 'O', 'P', 'L', 'A', 'N', '1'};
-constexpr uint32_t kVersion = 1;
+constexpr uint32_t kVersion = 2;
 constexpr uint32_t kByteOrder = 0x01020304u;
 
 // The scalar fields of a plan, as stored.
@@ -36,6 +39,8 @@ struct PlanScalars {
   double eps, sigma, kb_beta, sep_err, q_mean, plan_seconds, sur_warp_cycles,
       sur_residual_cycles, mean_bin_pts;
   int64_t grid_units, alpha_elems, beta_elems, cstart_elems, twiddle_elems, alg_bytes;
+  int32_t alpha_mode, has_rc_g;
+  int64_t rc_cols, rc_w_elems, rc_x_elems;
 };
 
 struct File {
@@ -120,13 +125,23 @@ fio_status save_plan(const fio_plan_s *p, const char *path) {
   sc.grid_units = p->grid_units; sc.alpha_elems = p->alpha_elems; sc.beta_elems = p->beta_elems;
   sc.cstart_elems = p->cstart_elems; sc.twiddle_elems = p->twiddle_elems;
   sc.alg_bytes = (int64_t)p->alg_bytes;
+  sc.alpha_mode = p->alpha_mode;
+  sc.has_rc_g = p->d_rc_g != nullptr;
+  sc.rc_cols = p->rc_cols; sc.rc_w_elems = p->rc_w_elems; sc.rc_x_elems = p->rc_x_elems;
+  const bool rc = p->alpha_mode == FIO_ALPHA_RECOMPUTE;
   const bool ok =
       put(fl.f, kMagic, 8) && put(fl.f, &kVersion, 4) && put(fl.f, &kByteOrder, 4) &&
       put(fl.f, &sc, sizeof(sc)) && put_vec(fl.f, p->wedges) && put_vec(fl.f, p->rows) &&
       put_vec(fl.f, p->ffts) && put_vec(fl.f, p->wedge_r) && put_vec(fl.f, p->wedge_err) &&
       put_vec(fl.f, p->pt_k1) && put_vec(fl.f, p->pt_k2) && put(fl.f, &p->horner, sizeof(p->horner)) &&
+      put_vec(fl.f, p->item_off) && put_vec(fl.f, p->bin_off) && put_vec(fl.f, p->bin1_off) &&
+      put_vec(fl.f, p->grp_first) && put(fl.f, &p->phase, sizeof(p->phase)) &&
       put_dev(fl.f, p->d_twiddle, (uint64_t)p->twiddle_elems * cs) &&
-      put_dev(fl.f, p->d_alpha, (uint64_t)p->alpha_elems * cs) &&
+      (rc || put_dev(fl.f, p->d_alpha, (uint64_t)p->alpha_elems * cs)) &&
+      (!rc || (put_dev(fl.f, p->d_rc_col, (uint64_t)p->rc_cols * sizeof(RcCol)) &&
+               put_dev(fl.f, p->d_rc_w, (uint64_t)p->rc_w_elems * cs) &&
+               (!p->d_rc_g || put_dev(fl.f, p->d_rc_g, (uint64_t)p->rc_cols * (2 * kTauMmax + 1) * 8)) &&
+               (!p->d_rc_x || put_dev(fl.f, p->d_rc_x, (uint64_t)p->rc_x_elems)))) &&
       put_dev(fl.f, p->d_beta, (uint64_t)p->beta_elems * cs) &&
       put_dev(fl.f, p->d_warp, LNN * sizeof(uint2)) && put_dev(fl.f, p->d_warps, LNN * sizeof(uint2)) &&
       put_dev(fl.f, p->d_perm, LNN * sizeof(uint32_t)) &&
@@ -159,7 +174,9 @@ fio_status load_plan(fio_plan_s *p, const char *path, int max_batch) {
   if (sc.N < 8 || sc.N > 2048 || sc.L < 1 || sc.L > 256 || (sc.precision != FIO_MIXED && sc.precision != FIO_FP64) ||
       sc.kb_w < 3 || sc.kb_w > kMaxKbWidth || sc.grid_units < 0 || sc.alpha_elems < 0 ||
       sc.beta_elems < 0 || sc.cstart_elems < 0 || sc.twiddle_elems < 0 || sc.n_items < 0 ||
-      sc.n_bins < 0 || sc.n_bins1 < 0) {
+      sc.n_bins < 0 || sc.n_bins1 < 0 ||
+      (sc.alpha_mode != FIO_ALPHA_STORED && sc.alpha_mode != FIO_ALPHA_RECOMPUTE) ||
+      sc.rc_cols < 0 || sc.rc_w_elems < 0 || sc.rc_x_elems < 0) {
     set_error("fio_plan_load: corrupt plan header");
     return FIO_EINVAL;
   }
@@ -168,8 +185,34 @@ fio_status load_plan(fio_plan_s *p, const char *path, int max_batch) {
                       get_vec(fl.f, p->rows, 1ull << 24) && get_vec(fl.f, p->ffts, 1ull << 16) &&
                       get_vec(fl.f, p->wedge_r, (uint64_t)sc.L) && get_vec(fl.f, p->wedge_err, (uint64_t)sc.L) &&
                       get_vec(fl.f, p->pt_k1, NN) && get_vec(fl.f, p->pt_k2, NN) &&
-                      get(fl.f, &p->horner, sizeof(p->horner));
-  if (!tables) {
+                      get(fl.f, &p->horner, sizeof(p->horner)) &&
+                      get_vec(fl.f, p->item_off, (uint64_t)sc.L + 1) &&
+                      get_vec(fl.f, p->bin_off, (uint64_t)sc.L + 1) &&
+                      get_vec(fl.f, p->bin1_off, (uint64_t)sc.L + 1) &&
+                      get_vec(fl.f, p->grp_first, (uint64_t)sc.L + 1) &&
+                      get(fl.f, &p->phase, sizeof(p->phase));
+  bool offsets = tables && p->item_off.size() == (size_t)sc.L + 1 &&
+                 p->bin_off.size() == (size_t)sc.L + 1 && p->bin1_off.size() == (size_t)sc.L + 1 &&
+                 p->item_off.back() == sc.n_items && p->bin_off.back() == sc.n_bins &&
+                 p->bin1_off.back() == sc.n_bins1;
+  for (int l = 0; offsets && l < sc.L; ++l)
+    offsets = p->item_off[l] <= p->item_off[l + 1] && p->bin_off[l] <= p->bin_off[l + 1] &&
+              p->bin1_off[l] <= p->bin1_off[l + 1] && p->item_off[l] >= 0 && p->bin_off[l] >= 0 &&
+              p->bin1_off[l] >= 0;
+  if (sc.alpha_mode == FIO_ALPHA_RECOMPUTE) {
+    offsets = offsets && p->grp_first.size() >= 2 && p->grp_first.front() == 0 &&
+              p->grp_first.back() == sc.L;
+    for (size_t g = 0; offsets && g + 1 < p->grp_first.size(); ++g)
+      offsets = p->grp_first[g] < p->grp_first[g + 1];
+    // every wedge's columns and V S^-1 lie inside the stored arrays
+    for (int l = 0; offsets && l < sc.L; ++l) {
+      const WedgeDev &w = p->wedges[l];
+      offsets = w.rc_r >= 0 && w.qp >= 0 && w.rc_col_off >= 0 && w.rc_w_off >= 0 &&
+                w.rc_col_off + w.rc_r <= sc.rc_cols &&
+                w.rc_w_off + (int64_t)w.rc_r * w.qp <= sc.rc_w_elems;
+    }
+  }
+  if (!tables || !offsets) {
     set_error("fio_plan_load: corrupt or truncated host tables");
     return FIO_EINVAL;
   }
@@ -185,11 +228,28 @@ fio_status load_plan(fio_plan_s *p, const char *path, int max_batch) {
   p->grid_units = sc.grid_units; p->alpha_elems = sc.alpha_elems; p->beta_elems = sc.beta_elems;
   p->cstart_elems = sc.cstart_elems; p->twiddle_elems = sc.twiddle_elems;
   p->alg_bytes = (unsigned long long)sc.alg_bytes;
+  p->alpha_mode = sc.alpha_mode;
+  p->rc_cols = sc.rc_cols; p->rc_w_elems = sc.rc_w_elems; p->rc_x_elems = sc.rc_x_elems;
+  const bool rc = p->alpha_mode == FIO_ALPHA_RECOMPUTE;
   cudaGetDevice(&p->device);
   const size_t cs = p->precision == FIO_FP64 ? 16 : 8;
   fio_status s;
   if ((s = get_dev(fl.f, &p->d_twiddle, (uint64_t)p->twiddle_elems * cs)) != FIO_OK) return s;
-  if ((s = get_dev(fl.f, &p->d_alpha, (uint64_t)p->alpha_elems * cs)) != FIO_OK) return s;
+  if (rc) {  // the regeneration buffer: allocated, not stored
+    if (cudaMalloc(&p->d_alpha, std::max<size_t>((size_t)p->alpha_elems * cs, 16)) != cudaSuccess) {
+      p->d_alpha = nullptr;
+      set_error("fio_plan_load: device allocation failed");
+      return FIO_ENOMEM;
+    }
+    if ((s = get_dev(fl.f, (void **)&p->d_rc_col, (uint64_t)p->rc_cols * sizeof(RcCol))) != FIO_OK) return s;
+    if ((s = get_dev(fl.f, &p->d_rc_w, (uint64_t)p->rc_w_elems * cs)) != FIO_OK) return s;
+    if (sc.has_rc_g &&
+        (s = get_dev(fl.f, &p->d_rc_g, (uint64_t)p->rc_cols * (2 * kTauMmax + 1) * 8)) != FIO_OK)
+      return s;
+    if (p->rc_x_elems > 0 && (s = get_dev(fl.f, &p->d_rc_x, (uint64_t)p->rc_x_elems)) != FIO_OK) return s;
+  } else if ((s = get_dev(fl.f, &p->d_alpha, (uint64_t)p->alpha_elems * cs)) != FIO_OK) {
+    return s;
+  }
   if ((s = get_dev(fl.f, &p->d_beta, (uint64_t)p->beta_elems * cs)) != FIO_OK) return s;
   if ((s = get_dev(fl.f, (void **)&p->d_warp, LNN * sizeof(uint2))) != FIO_OK) return s;
   if ((s = get_dev(fl.f, (void **)&p->d_warps, LNN * sizeof(uint2))) != FIO_OK) return s;
@@ -212,6 +272,15 @@ fio_status load_plan(fio_plan_s *p, const char *path, int max_batch) {
     return FIO_OK;
   };
   if ((s = upload((void **)&p->d_wedges, p->wedges.data(), p->wedges.size() * sizeof(WedgeDev))) != FIO_OK) return s;
+  if (rc) {
+    long long abuf = 0;
+    const std::vector<WedgeDev> wrc = rc_wedge_table(p->wedges, p->grp_first, (long long)NN, &abuf);
+    if (abuf != p->alpha_elems) {
+      set_error("fio_plan_load: corrupt plan header");
+      return FIO_EINVAL;
+    }
+    if ((s = upload((void **)&p->d_wedges_rc, wrc.data(), wrc.size() * sizeof(WedgeDev))) != FIO_OK) return s;
+  }
   if ((s = upload((void **)&p->d_rows, p->rows.data(), p->rows.size() * sizeof(RowDev))) != FIO_OK) return s;
   if ((s = upload((void **)&p->d_ffts, p->ffts.data(), p->ffts.size() * sizeof(FftPlanDev))) != FIO_OK) return s;
   const int zero = 0;
@@ -226,7 +295,7 @@ fio_status load_plan(fio_plan_s *p, const char *path, int max_batch) {
                    LNN * (2 * sizeof(uint2) + sizeof(uint32_t)) + p->cstart_elems * sizeof(int) +
                    p->n_items * sizeof(int4) + (p->n_bins + p->n_bins1) * sizeof(int2) +
                    p->wedges.size() * sizeof(WedgeDev) + p->rows.size() * sizeof(RowDev) +
-                   p->ffts.size() * sizeof(FftPlanDev) + gbytes + fbytes;
+                   p->ffts.size() * sizeof(FftPlanDev) + gbytes + fbytes + rc_bytes(p);
   return FIO_OK;
 }
 

@@ -263,7 +263,8 @@ k_spread_sweep(const float2 *__restrict__ gin, float2 *__restrict__ grid,
 // One launch over every bin of every wedge.  A pass covers chp = 32 UPL channels;
 // the chunk size kc fills the shared-memory budget.
 template <int W, int UPL>
-cudaError_t launch_sweep(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s) {
+cudaError_t launch_sweep(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s,
+                         const WorkRange &wr) {
   const long long NN = (long long)p->N * p->N;
   const int chp = 32 * UPL;
   int qpmax = 2;
@@ -276,10 +277,10 @@ cudaError_t launch_sweep(const fio_plan_s *p, const void *g, void *grid, int B, 
   cudaError_t e = cudaFuncSetAttribute(k_spread_sweep<W, UPL>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  if (p->n_bins1 > 0)
-    k_spread_sweep<W, UPL><<<p->n_bins1, kSwThreads, smem, s>>>(
-        (const float2 *)g, (float2 *)grid, p->d_wedges, p->d_bins1, p->d_cstart,
-        (const float2 *)p->d_alpha, p->d_warps, p->d_perm, NN, B, make_kbdev(p), p->horner, kc,
+  if (wr.n_bins1 > 0)
+    k_spread_sweep<W, UPL><<<wr.n_bins1, kSwThreads, smem, s>>>(
+        (const float2 *)g, (float2 *)grid, wr.wedges, wr.bins1, p->d_cstart,
+        (const float2 *)wr.alpha, p->d_warps, p->d_perm, NN, B, make_kbdev(p), p->horner, kc,
         chp, qpmax, nbmax, p->d_errword);
   return cudaGetLastError();
 }
@@ -287,39 +288,40 @@ cudaError_t launch_sweep(const fio_plan_s *p, const void *g, void *grid, int B, 
 // UPL = ceil(channels / 32) single-term units per lane (up to the register
 // limit; more channels take several passes).
 template <int W>
-cudaError_t sweep_w(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s) {
+cudaError_t sweep_w(const fio_plan_s *p, const void *g, void *grid, int B, cudaStream_t s,
+                    const WorkRange &wr) {
   int qpmax = 2;
   for (const WedgeDev &w : p->wedges) qpmax = std::max(qpmax, w.qp);
   const int nchmax = B * qpmax;
   if (nchmax >= (1 << 20)) return cudaErrorInvalidValue;  // the channel index divisions need < 2^20
   constexpr int UM = max_upl(W);
   switch (std::min(UM, (nchmax + 31) / 32)) {
-    case 1: return launch_sweep<W, 1>(p, g, grid, B, s);
-    case 2: return launch_sweep<W, std::min(UM, 2)>(p, g, grid, B, s);
-    case 3: return launch_sweep<W, std::min(UM, 3)>(p, g, grid, B, s);
-    case 4: return launch_sweep<W, std::min(UM, 4)>(p, g, grid, B, s);
-    case 5: return launch_sweep<W, std::min(UM, 5)>(p, g, grid, B, s);
-    case 6: return launch_sweep<W, std::min(UM, 6)>(p, g, grid, B, s);
-    case 7: return launch_sweep<W, std::min(UM, 7)>(p, g, grid, B, s);
-    default: return launch_sweep<W, std::min(UM, 8)>(p, g, grid, B, s);
+    case 1: return launch_sweep<W, 1>(p, g, grid, B, s, wr);
+    case 2: return launch_sweep<W, std::min(UM, 2)>(p, g, grid, B, s, wr);
+    case 3: return launch_sweep<W, std::min(UM, 3)>(p, g, grid, B, s, wr);
+    case 4: return launch_sweep<W, std::min(UM, 4)>(p, g, grid, B, s, wr);
+    case 5: return launch_sweep<W, std::min(UM, 5)>(p, g, grid, B, s, wr);
+    case 6: return launch_sweep<W, std::min(UM, 6)>(p, g, grid, B, s, wr);
+    case 7: return launch_sweep<W, std::min(UM, 7)>(p, g, grid, B, s, wr);
+    default: return launch_sweep<W, std::min(UM, 8)>(p, g, grid, B, s, wr);
   }
 }
 
 }  // namespace
 
 cudaError_t launch_spread_sweep(const fio_plan_s *p, const void *g, void *grid, int B,
-                                cudaStream_t s) {
+                                cudaStream_t s, const WorkRange &wr) {
   switch (p->kb.w) {
-    case 3: return sweep_w<3>(p, g, grid, B, s);
-    case 4: return sweep_w<4>(p, g, grid, B, s);
-    case 5: return sweep_w<5>(p, g, grid, B, s);
-    case 6: return sweep_w<6>(p, g, grid, B, s);
-    case 7: return sweep_w<7>(p, g, grid, B, s);
-    case 8: return sweep_w<8>(p, g, grid, B, s);
-    case 9: return sweep_w<9>(p, g, grid, B, s);
-    case 10: return sweep_w<10>(p, g, grid, B, s);
-    case 11: return sweep_w<11>(p, g, grid, B, s);
-    case 12: return sweep_w<12>(p, g, grid, B, s);
+    case 3: return sweep_w<3>(p, g, grid, B, s, wr);
+    case 4: return sweep_w<4>(p, g, grid, B, s, wr);
+    case 5: return sweep_w<5>(p, g, grid, B, s, wr);
+    case 6: return sweep_w<6>(p, g, grid, B, s, wr);
+    case 7: return sweep_w<7>(p, g, grid, B, s, wr);
+    case 8: return sweep_w<8>(p, g, grid, B, s, wr);
+    case 9: return sweep_w<9>(p, g, grid, B, s, wr);
+    case 10: return sweep_w<10>(p, g, grid, B, s, wr);
+    case 11: return sweep_w<11>(p, g, grid, B, s, wr);
+    case 12: return sweep_w<12>(p, g, grid, B, s, wr);
   }
   return cudaErrorNotSupported;
 }

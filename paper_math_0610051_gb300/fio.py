@@ -19,6 +19,7 @@ FIO_OK, FIO_EINVAL, FIO_ENOMEM, FIO_ECUDA, FIO_ERANK, FIO_ETIMEOUT, FIO_EUNSUPPO
 PHASE_SHIFT_WAVE, PHASE_ELLIPSE, PHASE_TAU_MODES, PHASE_ELLIPSE_PRODUCT = 0, 1, 2, 3
 AMP_ONE, AMP_SEPARABLE, AMP_HANKEL = 0, 1, 2
 MIXED, FP64 = 0, 1
+ALPHA_STORED, ALPHA_RECOMPUTE = 0, 1
 
 
 class FioError(RuntimeError):
@@ -41,7 +42,8 @@ class _Options(ctypes.Structure):
                 ("kb_width", ctypes.c_int), ("seed", ctypes.c_ulonglong), ("r0", ctypes.c_int),
                 ("rank_cap", ctypes.c_int), ("max_batch", ctypes.c_int),
                 ("surrogate", ctypes.c_void_p), ("surrogate_warp_budget", ctypes.c_double),
-                ("sep_cut", ctypes.c_double), ("sep_target", ctypes.c_double)]
+                ("sep_cut", ctypes.c_double), ("sep_target", ctypes.c_double),
+                ("alpha_mode", ctypes.c_int), ("alpha_group", ctypes.c_int)]
 
 
 class _SurInfo(ctypes.Structure):
@@ -66,7 +68,9 @@ class _PlanInfo(ctypes.Structure):
                 ("kernel_launches", ctypes.c_ulonglong), ("surrogate_warp", ctypes.c_int),
                 ("surrogate_warp_cycles", ctypes.c_double),
                 ("surrogate_residual_cycles", ctypes.c_double), ("max_bin_points", ctypes.c_int),
-                ("mean_bin_points", ctypes.c_double), ("max_spread_candidates", ctypes.c_int), ("sep_error", ctypes.c_double)]
+                ("mean_bin_points", ctypes.c_double), ("max_spread_candidates", ctypes.c_int),
+                ("sep_error", ctypes.c_double), ("alpha_mode", ctypes.c_int),
+                ("alpha_groups", ctypes.c_int), ("bytes_recompute", ctypes.c_ulonglong)]
 
 
 class _WedgeInfo(ctypes.Structure):
@@ -78,7 +82,8 @@ class _WedgeInfo(ctypes.Structure):
 
 # Every symbol include/fio.h declares (checked by the tests).
 EXPORTS = [
-    "fio_options_default", "fio_plan_create", "fio_apply", "fio_apply_adjoint", "fio_apply_normal",
+    "fio_options_default", "fio_plan_create", "fio_apply", "fio_apply_real", "fio_apply_adjoint",
+    "fio_apply_normal",
     "fio_apply_noalloc",
     "fio_plan_sync",
     "fio_plan_get_info", "fio_plan_get_wedge", "fio_plan_export_wedge", "fio_plan_export_warp",
@@ -106,6 +111,7 @@ def lib():
             L.fio_plan_create.argtypes = [I, ctypes.POINTER(_Phase), ctypes.POINTER(_Amp), D,
                                           ctypes.POINTER(_Options), ctypes.POINTER(P)]
             L.fio_apply.argtypes = [P, P, P, I, P]
+            L.fio_apply_real.argtypes = [P, P, P, I, P]
             L.fio_apply_adjoint.argtypes = [P, P, P, I, P]
             L.fio_apply_normal.argtypes = [P, P, P, I, P]
             L.fio_apply_noalloc.argtypes = [P, P, P, I, P]
@@ -178,7 +184,8 @@ class Plan:
                  L: int = 0, sigma: float = 0.0, kb_width: int = 0, seed: int = 0x5EED5EED,
                  r0: int = 0, rank_cap: int = 0, max_batch: int = 1, device=None,
                  surrogate: "Surrogate | None" = None, surrogate_warp_budget: float = 0.0,
-                 sep_cut: float = 0.0, sep_target: float = 0.0):
+                 sep_cut: float = 0.0, sep_target: float = 0.0, alpha_mode: str = "stored",
+                 alpha_group: int = 0):
         import torch
         self._torch = torch
         self.device = torch.device("cuda", torch.cuda.current_device() if device is None else device)
@@ -201,6 +208,8 @@ class Plan:
         opt.surrogate = surrogate._handle if surrogate is not None else None
         opt.surrogate_warp_budget = float(surrogate_warp_budget)
         opt.sep_cut, opt.sep_target = float(sep_cut), float(sep_target)
+        opt.alpha_mode = {"stored": ALPHA_STORED, "recompute": ALPHA_RECOMPUTE}.get(alpha_mode, alpha_mode)
+        opt.alpha_group = int(alpha_group)
         self._surrogate = surrogate
         self.N = int(N)
         self.precision = opt.precision
@@ -277,7 +286,25 @@ class Plan:
         return out
 
     def apply(self, f, out=None):
-        """out = L f (fio_apply); f: complex tensor [..., N, N] on the plan's device."""
+        """out = L f (fio_apply); f: complex tensor [..., N, N] on the plan's device.
+        A real f (float32 for mixed plans, float64 for FP64) goes through
+        fio_apply_real and gives the complex result of f + 0i."""
+        torch = self._torch
+        rdtype = torch.float64 if self.precision == FP64 else torch.float32
+        if isinstance(f, torch.Tensor) and f.dtype == rdtype:
+            if f.device != self.device or f.shape[-2:] != (self.N, self.N):
+                raise FioError(FIO_EINVAL, f"input must be a tensor on {self.device} ending with "
+                                           f"({self.N}, {self.N})")
+            x = f.resolve_neg().contiguous()
+            batch = x.numel() // (self.N * self.N)
+            if out is None:
+                out = torch.empty(x.shape, dtype=self.dtype, device=self.device)
+            elif out.shape != x.shape or out.dtype != self.dtype or not out.is_contiguous():
+                raise FioError(FIO_EINVAL, "out must be a contiguous complex tensor of f's shape")
+            _check(lib().fio_apply_real(self._handle, ctypes.c_void_p(x.data_ptr()),
+                                        ctypes.c_void_p(out.data_ptr()), int(batch),
+                                        _stream_ptr(torch, self.device)), "fio_apply_real")
+            return out
         return self._run(lib().fio_apply, f, out, "fio_apply")
 
     def adjoint(self, g, out=None):

@@ -276,6 +276,32 @@ def test_separation_error_estimator(env, orc, eps):
 
 # ----------------------------------------------------------- error paths -----
 
+@pytest.mark.parametrize("prec,eps", PREC_EPS)
+def test_real_input_entry(env, orc, prec, eps):
+    """fio_apply_real on a real batch against the O(N^4) oracle, and against
+    fio_apply on the same values as complex (the sum over wedges is an atomic
+    float sum, so the two agree to rounding, not bit for bit)."""
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    N, B = 48, 3
+    prm = synth.ellipse_params()
+    f = synth.white_noise(N, B, seed=12).real
+    rdt = torch.float64 if prec == "fp64" else torch.float32
+    with fio.Plan(N, fio.PHASE_ELLIPSE, prm, eps, precision=prec, max_batch=B) as plan:
+        fr = torch.from_numpy(np.ascontiguousarray(f)).to(rdt).cuda()
+        out_r = plan.apply(fr).cpu().numpy()
+        out_c = plan.apply(dev(torch, f, prec)).cpu().numpy()
+        assert out_r.dtype == (np.complex128 if prec == "fp64" else np.complex64)
+        # an output that overlaps the real input is refused before any launch
+        buf = torch.zeros(B * N * N, dtype=plan.dtype, device="cuda")
+        tail = torch.view_as_real(buf).view(-1)[B * N * N:]
+        st = fio.lib().fio_apply_real(plan._handle, tail.data_ptr(), buf.data_ptr(), B, None)
+        assert st == fio.FIO_EINVAL
+    ref = orc.apply_dense(orc.Phase(orc.ELLIPSE, prm), orc.Amplitude(), f[1])
+    assert rel(ref, out_r[1]) < eps
+    assert rel(out_c, out_r) < (1e-12 if prec == "fp64" else 1e-6)
+
+
 def test_batch_limit_and_dtype_errors(env):
     fio, torch = env
     from paper_math_0610051_gb300 import synth

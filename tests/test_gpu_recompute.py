@@ -1,0 +1,159 @@
+"""The recompute storage mode (Sec. 3.2, Eq. probnewfac): gamma^x = A_[C] V S^-1
+formed again in every apply from the sampled columns and V S^-1, instead of
+being stored for every x.
+
+The plan's randomized separation does not depend on the mode (same seed, same
+samples, same V S^-1), so a recompute plan must apply the stored plan's
+operator: complex64 plans form the entries A_{x, xi_c} in single precision
+from cancellation-free forms of the residual phase (relative rounding about
+1e-7 per entry, 2e-6 allowed over a whole output), FP64 plans with the plan's
+own FP64 evaluation (1e-12).  Against the oracle the bar is the method's own:
+eps.
+"""
+import os
+
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_math_0610051_gb300 import fio
+    return fio, torch
+
+
+def rel(ref, got):
+    ref, got = np.asarray(ref).ravel(), np.asarray(got).ravel()
+    return float(np.linalg.norm(ref - got) / np.linalg.norm(ref))
+
+
+def _cases():
+    from paper_math_0610051_gb300 import fio, synth
+    return {
+        "ellipse": (fio.PHASE_ELLIPSE, synth.ellipse_params(), None),
+        "ellipse_product": (fio.PHASE_ELLIPSE_PRODUCT, synth.paper_ellipse_params(), None),
+        "tau_separable": (fio.PHASE_TAU_MODES, synth.tau_mode_params(32, seed=3), (0.5, 0.3)),
+        "wave": (fio.PHASE_SHIFT_WAVE, np.array([3 / 64, -5 / 64, 0.15]), None),
+    }
+
+
+@pytest.mark.parametrize("name", ["ellipse", "ellipse_product", "tau_separable", "wave"])
+@pytest.mark.parametrize("prec,eps,tol", [("mixed", 1e-4, 2e-6), ("fp64", 1e-6, 1e-12)])
+def test_recompute_matches_stored(env, orc, name, prec, eps, tol):
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    kind, prm, amp = _cases()[name]
+    N, B = 64, 2
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    f = torch.from_numpy(synth.white_noise(N, B, seed=21, real=False)).to(dt).cuda()
+    out = {}
+    for mode in ("stored", "recompute"):
+        with fio.Plan(N, kind, prm, eps, amp=amp, precision=prec, max_batch=B, alpha_mode=mode,
+                      alpha_group=3) as plan:
+            info = plan.info()
+            out[mode] = (plan.apply(f).cpu().numpy(), plan.adjoint(f).cpu().numpy(), info)
+            plan.sync()
+    (fs, as_, i_s), (fr, ar, i_r) = out["stored"], out["recompute"]
+    assert i_r["alpha_mode"] == fio.ALPHA_RECOMPUTE and i_s["alpha_mode"] == fio.ALPHA_STORED
+    assert i_r["q_mean"] == i_s["q_mean"] and i_r["sep_error"] == i_s["sep_error"]
+    assert i_r["alpha_groups"] == -(-i_r["L"] // 3)
+    assert rel(fs, fr) < tol and rel(as_, ar) < tol, (rel(fs, fr), rel(as_, ar))
+    a = orc.Amplitude() if amp is None else orc.Amplitude(orc.AMP_SEPARABLE, *amp)
+    okind = {fio.PHASE_ELLIPSE: orc.ELLIPSE, fio.PHASE_ELLIPSE_PRODUCT: orc.ELLIPSE_PRODUCT,
+             fio.PHASE_TAU_MODES: orc.TAU_MODES, fio.PHASE_SHIFT_WAVE: orc.SHIFT_WAVE}[kind]
+    ref = orc.apply_dense(orc.Phase(okind, prm), a, f.cpu().numpy()[1])
+    assert rel(ref, fr[1]) < eps
+
+
+def test_recompute_storage_and_groups(env):
+    """The buffer holds one group's factors; the plan's factor bytes fall by the
+    ratio of groups, and the kept tables are a small part of the stored gamma^x."""
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    N = 256
+    with fio.Plan(N, fio.PHASE_ELLIPSE, synth.ellipse_params(), 1e-4) as ps:
+        st = ps.info()
+    with fio.Plan(N, fio.PHASE_ELLIPSE, synth.ellipse_params(), 1e-4, alpha_mode="recompute",
+                  alpha_group=2) as pr:
+        rc = pr.info()
+    L = st["L"]
+    assert rc["alpha_groups"] == L // 2
+    assert rc["bytes_alpha"] <= st["bytes_alpha"] * 2 / L * 1.5
+    assert rc["bytes_recompute"] < st["bytes_alpha"] / 20
+    assert rc["bytes_total"] < st["bytes_total"] - st["bytes_alpha"] / 2
+    print(f"\nN={N}: stored gamma^x {st['bytes_alpha'] / 1e6:.1f} MB; recompute buffer "
+          f"{rc['bytes_alpha'] / 1e6:.1f} MB + tables {rc['bytes_recompute'] / 1e6:.2f} MB")
+
+
+@pytest.mark.parametrize("prec,eps", [("mixed", 1e-4), ("fp64", 1e-6)])
+def test_recompute_sampled_against_oracle(env, orc, prec, eps):
+    """N = 512, the ellipse phase: forward at 256 random x and the adjoint's
+    spectrum at 128 random xi against the oracle's direct sums."""
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    N = 512
+    prm = synth.ellipse_params()
+    ph = orc.Phase(orc.ELLIPSE, prm)
+    f = synth.white_noise(N, 1, seed=5)
+    g = synth.white_noise(N, 1, seed=6, real=False)
+    dt = torch.complex128 if prec == "fp64" else torch.complex64
+    with fio.Plan(N, fio.PHASE_ELLIPSE, prm, eps, precision=prec, alpha_mode="recompute") as plan:
+        out = plan.apply(torch.from_numpy(f).to(dt).cuda()).cpu().numpy()[0]
+        adj = plan.adjoint(torch.from_numpy(g).to(dt).cuda()).cpu().numpy()[0]
+    n1, n2 = synth.sample_points(N, 256, seed=8)
+    ref = orc.apply_points(ph, orc.Amplitude(), orc.dft2(f[0]), n1, n2)
+    assert rel(ref, out[n1, n2]) < eps
+    gen = np.random.default_rng(9)
+    k1, k2 = gen.integers(-N // 2, N // 2, 128), gen.integers(-N // 2, N // 2, 128)
+    aref = orc.adjoint_hat_points(ph, orc.Amplitude(), g[0], k1, k2)
+    spec = orc.dft2(adj.astype(np.complex128))
+    assert rel(aref, spec[k1 + N // 2, k2 + N // 2]) < eps
+
+
+def test_recompute_save_load(env, tmp_path):
+    """A recompute plan survives fio_plan_save / fio_plan_load: the loaded plan's
+    adjoint is bit-identical, its forward equal up to the atomic wedge sum."""
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    N, B = 64, 2
+    path = os.path.join(tmp_path, "rc.fioplan")
+    f = torch.from_numpy(synth.white_noise(N, B, seed=4, real=False)).to(torch.complex64).cuda()
+    prm = synth.tau_mode_params(16, seed=2)
+    with fio.Plan(N, fio.PHASE_TAU_MODES, prm, 1e-4, max_batch=B, alpha_mode="recompute",
+                  alpha_group=5) as plan:
+        ref_f, ref_a = plan.apply(f).cpu().numpy(), plan.adjoint(f).cpu().numpy()
+        plan.save(path)
+    with fio.Plan.load(path) as p2:
+        info = p2.info()
+        got_f, got_a = p2.apply(f).cpu().numpy(), p2.adjoint(f).cpu().numpy()
+    assert info["alpha_mode"] == fio.ALPHA_RECOMPUTE and info["alpha_groups"] >= 2
+    assert np.array_equal(ref_a, got_a)
+    assert rel(ref_f, got_f) < 1e-6
+
+
+@pytest.mark.gpu_long
+def test_recompute_N2048_forward_sampled(env, orc):
+    """N = 2048 in the recompute mode: the stored gamma^x would take about
+    29 GB; the forward at 256 random x against the oracle's direct sums."""
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    N = 2048
+    prm = synth.ellipse_params()
+    f = synth.white_noise(N, 1, seed=15)
+    with fio.Plan(N, fio.PHASE_ELLIPSE, prm, 1e-4, alpha_mode="recompute", alpha_group=4) as plan:
+        info = plan.info()
+        out = plan.apply(torch.from_numpy(f).to(torch.complex64).cuda()).cpu().numpy()[0]
+    n1, n2 = synth.sample_points(N, 256, seed=16)
+    ref = orc.apply_points(orc.Phase(orc.ELLIPSE, prm), orc.Amplitude(), orc.dft2(f[0]), n1, n2)
+    err = rel(ref, out[n1, n2])
+    print(f"\nN=2048 recompute: L={info['L']} q mean {info['q_mean']:.1f} plan {info['plan_seconds']:.0f} s "
+          f"bytes total {info['bytes_total'] / 1e9:.2f} GB (buffer {info['bytes_alpha'] / 1e9:.2f} GB), "
+          f"rel-L2 {err:.2e}")
+    assert err < 1e-4

@@ -226,6 +226,34 @@ def test_plan_create_rejects_bad_arguments_before_cuda(fio):
     assert create(64, bad, kind=fio.PHASE_ELLIPSE_PRODUCT)[0] == fio.FIO_EINVAL
 
 
+def test_alpha_mode_options_are_validated_before_cuda(fio):
+    """An unknown storage mode or a negative group size is FIO_EINVAL; the
+    recompute mode of a complex64 plan with the Hankel amplitude is
+    FIO_EUNSUPPORTED; all before any CUDA call."""
+    lib = fio.lib()
+    prm = np.array([2 / 3, 1 / 3, 2 / 3, 1 / 3])
+    ph = fio._Phase(fio.PHASE_ELLIPSE, 0, prm.ctypes.data_as(ctypes.POINTER(ctypes.c_double)))
+
+    def create(mode, group=0, amp=None, precision=fio.MIXED):
+        opt = fio._Options()
+        lib.fio_options_default(ctypes.byref(opt))
+        opt.alpha_mode, opt.alpha_group, opt.precision = mode, group, precision
+        h = ctypes.c_void_p()
+        st = lib.fio_plan_create(64, ctypes.byref(ph), ctypes.byref(amp) if amp else None, 1e-4,
+                                 ctypes.byref(opt), ctypes.byref(h))
+        return st, h.value
+
+    opt = fio._Options()
+    assert lib.fio_options_default(ctypes.byref(opt)) == fio.FIO_OK
+    assert opt.alpha_mode == fio.ALPHA_STORED and opt.alpha_group == 0
+    assert create(2) == (fio.FIO_EINVAL, None)
+    assert create(-1) == (fio.FIO_EINVAL, None)
+    assert create(fio.ALPHA_RECOMPUTE, group=-3) == (fio.FIO_EINVAL, None)
+    hank = fio._Amp(fio.AMP_HANKEL, 1.0, 0.0)
+    assert create(fio.ALPHA_RECOMPUTE, amp=hank) == (fio.FIO_EUNSUPPORTED, None)
+    assert b"FP64" in lib.fio_last_error()
+
+
 def test_hankel_amplitude_sign_is_validated(fio):
     """FIO_AMP_HANKEL takes its sign from a1, which must be +1 or -1."""
     lib = fio.lib()

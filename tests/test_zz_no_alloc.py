@@ -57,6 +57,24 @@ def test_noalloc_matches_apply_twice(env, prec):
         plan.sync()
 
 
+def test_noalloc_on_a_recompute_plan(env):
+    """A plan in the recompute storage mode forms gamma^x in its own buffer, so
+    the no-allocation entry still allocates nothing and agrees with fio_apply."""
+    fio, torch = env
+    from paper_math_0610051_gb300 import synth
+    N, B = 64, 2
+    with fio.Plan(N, fio.PHASE_ELLIPSE, synth.ellipse_params(), 1e-4, max_batch=B,
+                  alpha_mode="recompute") as plan:
+        f = torch.from_numpy(synth.white_noise(N, B, seed=7, real=False)).to(torch.complex64).cuda()
+        ref = plan.apply(f)
+        out = torch.full_like(f, float("nan"))
+        assert _noalloc(fio, torch, plan, f, out) == fio.FIO_OK
+        torch.cuda.synchronize()
+        err = (torch.linalg.vector_norm(out - ref) / torch.linalg.vector_norm(ref)).item()
+        assert err <= 1e-6, err
+        plan.sync()
+
+
 def test_noalloc_rejects_oversize(env):
     fio, torch = env
     from paper_math_0610051_gb300 import synth
