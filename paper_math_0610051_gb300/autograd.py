@@ -2,8 +2,9 @@
 
 For a complex-linear operator y = L f, PyTorch's vector-Jacobian product is
 L^H applied to the incoming gradient, and L^H is exactly what the library's
-adjoint computes for the fast operator (Sec. 3.5).  Real inputs are handled by
-PyTorch's own complex <-> real rules (pass ``f.to(plan.dtype)``).
+adjoint computes for the fast operator (Sec. 3.5).  A real f goes through the
+real-input forward (fio_apply_real); its gradient is the real part of L^H
+applied to the incoming gradient, as PyTorch's real-to-complex rule gives.
 """
 from __future__ import annotations
 
@@ -16,11 +17,13 @@ class FIOApply(torch.autograd.Function):
     @staticmethod
     def forward(ctx, f, plan):
         ctx.plan = plan
+        ctx.real = not f.is_complex()
         return plan.apply(f.contiguous())
 
     @staticmethod
     def backward(ctx, grad_out):
-        return ctx.plan.adjoint(grad_out.contiguous()), None
+        g = ctx.plan.adjoint(grad_out.contiguous())
+        return (g.real.contiguous() if ctx.real else g), None
 
 
 class FIOAdjoint(torch.autograd.Function):

@@ -3,12 +3,12 @@
 // device memory while they run (see include/fio.h).
 //
 // The scratch is one file-scope __device__ array.  Host code cannot use the
-// array's name as a device address (on the host it is only a stand-in), so the
-// first call on each device, with that device current, asks the runtime for
-// the array's device address once and keeps it.
+// array's name as a device address (on the host it is only a stand-in), so
+// every call asks the runtime for the array's address on the current device.
+// The query allocates nothing, and it stays right after a device reset or a
+// new context, where the module (and so the array) is loaded again.
 #include <cuda_runtime.h>
 
-#include <mutex>
 #include <string>
 
 #include "fio_internal.h"
@@ -16,24 +16,12 @@
 namespace {
 
 constexpr size_t kScratchBytes = FIO_NOALLOC_SCRATCH_BYTES;
-constexpr int kMaxDevices = 64;
 
 __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
-std::mutex g_mutex;
-void *g_scratch_addr[kMaxDevices] = {};
-
-// Device address of the scratch array on the current device (set-up on first use).
-cudaError_t scratch_address(int dev, void **addr) {
-  std::lock_guard<std::mutex> lock(g_mutex);
-  if (!g_scratch_addr[dev]) {
-    void *ptr = nullptr;
-    const cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
-    if (e != cudaSuccess) return e;
-    g_scratch_addr[dev] = ptr;
-  }
-  *addr = g_scratch_addr[dev];
-  return cudaSuccess;
+// Device address of the scratch array on the current device.
+cudaError_t scratch_address(void **addr) {
+  return cudaGetSymbolAddress(addr, g_noalloc_scratch);
 }
 
 }  // namespace
@@ -60,12 +48,12 @@ extern "C" fio_status fio_apply_noalloc(fio_plan p, const void *f, void *out, in
   }
   int dev = -1;
   cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess || dev != p->device || dev < 0 || dev >= kMaxDevices) {
+  if (e != cudaSuccess || dev != p->device || dev < 0) {
     fio::set_error("fio_apply_noalloc: the plan's device must be the current device");
     return e != cudaSuccess ? FIO_ECUDA : FIO_EINVAL;
   }
   void *base = nullptr;
-  e = scratch_address(dev, &base);
+  e = scratch_address(&base);
   if (e != cudaSuccess) {
     fio::set_error(std::string("fio_apply_noalloc: cudaGetSymbolAddress: ") + cudaGetErrorString(e));
     return FIO_ECUDA;

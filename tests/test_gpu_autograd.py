@@ -110,3 +110,32 @@ def test_adjoint_function_gradient(env):
     e = (g.grad - lu).abs().max().item() / lu.abs().max().item()
     plan.close()
     assert e < 1e-12
+
+
+def test_real_input_gradient(env):
+    """A real f goes through fio_apply_real; its gradient is the real part of
+    the complex path's gradient (PyTorch's real-to-complex rule), and a central
+    difference of the quadratic loss along a real direction matches it."""
+    fio, ag, torch = env
+    from paper_math_0610051_gb300 import synth
+    N = 64
+    plan = fio.Plan(N, fio.PHASE_ELLIPSE, synth.ellipse_params(), 1e-6, precision="fp64")
+    g = torch.from_numpy(synth.white_noise(N, 1, seed=3, real=False)).cuda()
+    fr = torch.from_numpy(synth.white_noise(N, 1, seed=4).real.copy()).cuda().requires_grad_(True)
+    fc = fr.detach().to(torch.complex128).requires_grad_(True)
+
+    def loss(f):
+        return ((ag.fio_apply(f, plan) - g).abs() ** 2).sum()
+
+    loss(fr).backward()
+    loss(fc).backward()
+    assert fr.grad.dtype == torch.float64
+    e = (fr.grad - fc.grad.real).abs().max().item() / fc.grad.real.abs().max().item()
+    assert e < 1e-12
+    d = torch.from_numpy(np.random.default_rng(5).standard_normal((1, N, N))).cuda()
+    h = 1e-3
+    with torch.no_grad():
+        fd = (loss(fr + h * d) - loss(fr - h * d)).item() / (2 * h)
+    dd = (fr.grad * d).sum().item()
+    plan.close()
+    assert abs(fd - dd) <= 1e-9 * abs(dd)
