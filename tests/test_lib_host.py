@@ -373,8 +373,36 @@ def test_plan_load_rejects_bad_files_without_a_gpu(fio, tmp_path):
     short = os.path.join(tmp_path, "short.fioplan")
     with open(short, "wb") as fh:
         fh.write(b"FIOPLAN1" + (1).to_bytes(4, "little"))
-    for path in (bad, short, os.path.join(tmp_path, "missing.fioplan")):
+    # a file of the previous format version, and a current header whose storage
+    # mode is unknown: both rejected from the header alone
+    import struct
+
+    def header(version, alpha_mode):
+        ints = [64, 8, 0, 1, 6, 10, 8, 64, 0, 100, 500, 10, 10, 10, 40, 0]
+        dbl = [1e-4, 2.0, 14.0, 5e-5, 9.0, 1.0, 0.0, 0.0, 50.0]
+        i64 = [1000, 1000, 1000, 1000, 100, 1000]
+        return (b"FIOPLAN1" + struct.pack("<II", version, 0x01020304) +
+                struct.pack("<16i9d6q", *ints, *dbl, *i64) +
+                struct.pack("<2i3q", alpha_mode, 0, 0, 0, 0))
+
+    old_ver = os.path.join(tmp_path, "v1.fioplan")
+    with open(old_ver, "wb") as fh:
+        fh.write(header(1, 0))
+    bad_mode = os.path.join(tmp_path, "mode.fioplan")
+    with open(bad_mode, "wb") as fh:
+        fh.write(header(2, 7))
+    for path in (bad, short, os.path.join(tmp_path, "missing.fioplan"), old_ver, bad_mode):
         h = ctypes.c_void_p(1)
         assert lib.fio_plan_load(os.fsencode(path), 0, ctypes.byref(h)) == fio.FIO_EINVAL
         assert not h.value
         assert b"fio_plan_load" in lib.fio_last_error()
+    assert b"corrupt plan header" in lib.fio_last_error()
+    # control: the same header with a valid mode passes the header checks and
+    # stops at the missing tables, so the check above is the mode's
+    good_mode = os.path.join(tmp_path, "good.fioplan")
+    with open(good_mode, "wb") as fh:
+        fh.write(header(2, fio.ALPHA_RECOMPUTE))
+    h = ctypes.c_void_p(1)
+    assert lib.fio_plan_load(os.fsencode(good_mode), 0, ctypes.byref(h)) == fio.FIO_EINVAL
+    assert not h.value
+    assert b"host tables" in lib.fio_last_error()
