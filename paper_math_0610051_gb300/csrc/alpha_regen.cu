@@ -39,8 +39,9 @@ namespace {
 constexpr int kRgThreads = 256;
 
 // Terms t0 .. t0 + QC - 1 of every point: acc_t = sum_k A(x, xi_k) W[k][t].
-template <int QC>
-__global__ void __launch_bounds__(kRgThreads)
+// KIND: the phase kind (only the tau kind holds the 17 C_m(x) in registers).
+template <int QC, int KIND>
+__global__ void __launch_bounds__(kRgThreads, 2)
 k_regen_f32(PhaseDev ph, int N, const WedgeDev *__restrict__ Wd, int l0, int L,
             const uint2 *__restrict__ warps, const uint32_t *__restrict__ perm,
             const RcCol *__restrict__ cols, const float2 *__restrict__ G,
@@ -64,46 +65,66 @@ k_regen_f32(PhaseDev ph, int N, const WedgeDev *__restrict__ Wd, int l0, int L,
   if (ph.amp_kind == FIO_AMP_SEPARABLE)
     ax = 1.0f + (float)ph.a1 * sinpif(2.0f * (float)(x / N) / (float)N);
   float ea = 0.f, eb = 0.f, rho = 0.f;
-  float2 C[pe::kNm];
-  if (ph.kind == FIO_PHASE_ELLIPSE) {
+  float2 C[KIND == FIO_PHASE_TAU_MODES ? pe::kNm : 1];
+  if constexpr (KIND == FIO_PHASE_ELLIPSE) {
     const float2 v = xf[x];
     ea = v.x;
     eb = v.y;
     float st, ct;
     sincospif(2.0f * (float)l / (float)L, &st, &ct);
     rho = sqrtf(ea * ct * ct + eb * st * st);
-  } else if (ph.kind == FIO_PHASE_TAU_MODES) {
+  } else if constexpr (KIND == FIO_PHASE_TAU_MODES) {
 #pragma unroll
     for (int m = 0; m < pe::kNm; ++m) C[m] = xf[x * pe::kNm + m];
   }
   const RcCol *cl = cols + w.rc_col_off;
   const float2 *gl = G ? G + w.rc_col_off * pe::kNm : nullptr;
   float2 *out = alpha + w.alpha_off + pos * w.qp;
+  // A(x, xi_k) for column k: amplitude times exp(2 pi i Phi_l)
+  auto entry = [&](int k) -> float2 {
+    const RcCol c = cl[k];
+    float R = 0.f;
+    if constexpr (KIND == FIO_PHASE_ELLIPSE) {
+      const float psi = sqrtf(ea * c.fk1 * c.fk1 + eb * c.fk2 * c.fk2);
+      const float den = rho * (psi * rho + ea * c.ctk1 + eb * c.stk2);
+      R = den > 0.f ? __fdividef(ea * eb * c.cross2, den) : 0.f;  // xi = 0: Phi_l = 0
+    } else if constexpr (KIND == FIO_PHASE_TAU_MODES) {
+      const float2 *gk = gl + (long long)k * pe::kNm;
+#pragma unroll
+      for (int m = 0; m < pe::kNm; ++m) {
+        const float2 g = gk[m];
+        R = fmaf(C[m].x, g.x, fmaf(-C[m].y, g.y, R));
+      }
+    } else {
+      R = c.rsw;
+    }
+    float s, co;
+    sincospif(2.0f * R, &s, &co);
+    const float amp = ax * c.ampc;
+    return make_float2(amp * co, amp * s);
+  };
   for (int t0 = 0; t0 < w.qp; t0 += QC) {
     float2 acc[QC];
 #pragma unroll
     for (int j = 0; j < QC; ++j) acc[j] = make_float2(0.f, 0.f);
-    for (int k = 0; k < w.rc_r; ++k) {
-      const RcCol c = cl[k];
-      float R = 0.f;
-      if (ph.kind == FIO_PHASE_ELLIPSE) {
-        const float psi = sqrtf(ea * c.fk1 * c.fk1 + eb * c.fk2 * c.fk2);
-        const float den = rho * (psi * rho + ea * c.ctk1 + eb * c.stk2);
-        R = den > 0.f ? ea * eb * c.cross2 / den : 0.f;  // xi = 0: Phi_l = 0
-      } else if (ph.kind == FIO_PHASE_TAU_MODES) {
-        const float2 *gk = gl + (long long)k * pe::kNm;
+    // two columns per step, so that one entry's phase and sine overlap the other's
+    int k = 0;
+    for (; k + 1 < w.rc_r; k += 2) {
+      const float2 e0 = entry(k), e1 = entry(k + 1);
+      const float2 *wr = Wm + w.rc_w_off + (long long)k * w.qp + t0;
 #pragma unroll
-        for (int m = 0; m < pe::kNm; ++m) {
-          const float2 g = gk[m];
-          R = fmaf(C[m].x, g.x, fmaf(-C[m].y, g.y, R));
+      for (int j = 0; j < QC; ++j) {
+        if (t0 + j < w.qp) {
+          const float2 v0 = wr[j], v1 = wr[w.qp + j];
+          acc[j].x = fmaf(e0.x, v0.x, fmaf(-e0.y, v0.y, acc[j].x));
+          acc[j].y = fmaf(e0.x, v0.y, fmaf(e0.y, v0.x, acc[j].y));
+          acc[j].x = fmaf(e1.x, v1.x, fmaf(-e1.y, v1.y, acc[j].x));
+          acc[j].y = fmaf(e1.x, v1.y, fmaf(e1.y, v1.x, acc[j].y));
         }
-      } else {
-        R = c.rsw;
       }
-      float s, co;
-      sincospif(2.0f * R, &s, &co);
-      const float amp = ax * c.ampc;
-      const float2 e = make_float2(amp * co, amp * s);
+    }
+    if (k < w.rc_r) {
+      const float2 e = entry(k);
       const float2 *wr = Wm + w.rc_w_off + (long long)k * w.qp + t0;
 #pragma unroll
       for (int j = 0; j < QC; ++j) {
@@ -192,11 +213,17 @@ cudaError_t regen_alpha(const fio_plan_s *p, int g, cudaStream_t s) {
     k_regen_f64<8><<<grid, kRgThreads, 0, s>>>(p->phase, p->N, p->d_wedges_rc, l0, p->d_warps,
                                               p->d_perm, p->d_rc_col, (const double2 *)p->d_rc_w,
                                               p->d_rc_x, (double2 *)p->d_alpha);
-  else
-    k_regen_f32<24><<<grid, kRgThreads, 0, s>>>(
-        p->phase, p->N, p->d_wedges_rc, l0, p->L, p->d_warps, p->d_perm, p->d_rc_col,
-        (const float2 *)p->d_rc_g, (const float2 *)p->d_rc_w, (const float2 *)p->d_rc_x,
-        (float2 *)p->d_alpha);
+  else {
+    auto go = [&](auto kern) {
+      kern<<<grid, kRgThreads, 0, s>>>(p->phase, p->N, p->d_wedges_rc, l0, p->L, p->d_warps,
+                                        p->d_perm, p->d_rc_col, (const float2 *)p->d_rc_g,
+                                        (const float2 *)p->d_rc_w, (const float2 *)p->d_rc_x,
+                                        (float2 *)p->d_alpha);
+    };
+    if (p->phase.kind == FIO_PHASE_ELLIPSE) go(k_regen_f32<24, FIO_PHASE_ELLIPSE>);
+    else if (p->phase.kind == FIO_PHASE_TAU_MODES) go(k_regen_f32<24, FIO_PHASE_TAU_MODES>);
+    else go(k_regen_f32<24, FIO_PHASE_SHIFT_WAVE>);
+  }
   return cudaGetLastError();
 }
 

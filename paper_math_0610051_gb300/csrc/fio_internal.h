@@ -55,7 +55,7 @@ struct WedgeDev {
 // One sampled column xi_c of a wedge in the recompute storage mode: the values
 // the regeneration of gamma^x needs that do not depend on x, made in FP64 on
 // the host (rounded to float for complex64 plans).
-struct RcCol {
+struct alignas(16) RcCol {
   int k1, k2;      // the frequency xi_c
   float ctk1;      // cos(theta_l) k1 (theta_l: the wedge's centre direction)
   float stk2;      // sin(theta_l) k2
@@ -142,7 +142,8 @@ struct fio_plan_s {
   fio::RowDev *d_rows = nullptr;
   fio::FftPlanDev *d_ffts = nullptr;
   void *d_twiddle = nullptr;      // complex (float2 / double2) exp(-2 pi i k/n) tables
-  void *d_alpha = nullptr;        // gamma^x * centre phase / N, [l][pos][t] (sorted point order)
+  void *d_alpha = nullptr;        // gamma^x * centre phase / N, [l][pos][t] (sorted point order);
+                                  // recompute mode: the buffer of one group of wedges
   void *d_beta = nullptr;         // gamma^xi / phihat, [l][t][p]
   uint2 *d_warp = nullptr;        // warped points y' mod 1 as 32-bit fractions, [l][x]
   uint2 *d_warps = nullptr;       // the same in sorted point order, [l][pos]
