@@ -211,6 +211,21 @@ fio_status load_plan(fio_plan_s *p, const char *path, int max_batch) {
                 w.rc_col_off + w.rc_r <= sc.rc_cols &&
                 w.rc_w_off + (int64_t)w.rc_r * w.qp <= sc.rc_w_elems;
     }
+    // the phase and the per-x data the regeneration reads agree with each other:
+    // complex64 plans keep float2 per x (ellipse) or per (x, m) (tau modes) and
+    // the tau column factors; FP64 plans keep the plan's own FP64 phase data
+    const PhaseDev &ph = p->phase;
+    const bool kind_ok = ph.kind == FIO_PHASE_SHIFT_WAVE || ph.kind == FIO_PHASE_ELLIPSE ||
+                         ph.kind == FIO_PHASE_TAU_MODES;
+    const bool amp_ok = ph.amp_kind == FIO_AMP_ONE || ph.amp_kind == FIO_AMP_SEPARABLE ||
+                        (ph.amp_kind == FIO_AMP_HANKEL && sc.precision == FIO_FP64);
+    const int64_t per_x = ph.kind == FIO_PHASE_ELLIPSE ? 1
+                          : ph.kind == FIO_PHASE_TAU_MODES ? 2 * kTauMmax + 1 : 0;
+    const int64_t want_x = sc.precision == FIO_FP64 ? (per_x ? (int64_t)NN * per_x * 16 : 16)
+                                                    : (int64_t)NN * per_x * 8;
+    const bool want_g = sc.precision == FIO_MIXED && ph.kind == FIO_PHASE_TAU_MODES;
+    offsets = offsets && kind_ok && amp_ok && sc.rc_x_elems == want_x &&
+              (sc.has_rc_g != 0) == want_g;
   }
   if (!tables || !offsets) {
     set_error("fio_plan_load: corrupt or truncated host tables");
