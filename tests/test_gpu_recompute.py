@@ -141,7 +141,7 @@ def test_recompute_save_load(env, tmp_path):
 @pytest.mark.gpu_long
 def test_recompute_N2048_forward_sampled(env, orc):
     """N = 2048 in the recompute mode: the stored gamma^x would take about
-    29 GB; the forward at 256 random x against the oracle's direct sums."""
+    25 GB; the forward at 256 random x against the oracle's direct sums."""
     fio, torch = env
     from paper_math_0610051_gb300 import synth
     N = 2048
