@@ -521,3 +521,12 @@ def host_svd_right(R: np.ndarray):
     V = np.empty((n, n), np.complex128)
     _check(lib().fio_host_svd_right(n, _np_ptr(R), _np_ptr(s), _np_ptr(V)), "fio_host_svd_right")
     return s, V
+
+
+def __getattr__(name):
+    """fio.FIOApply / fio.FIOAdjoint: the autograd functions of autograd.py, imported
+    on first use (they need torch, which this module imports only with a plan)."""
+    if name in ("FIOApply", "FIOAdjoint", "fio_apply", "fio_adjoint"):
+        from . import autograd
+        return getattr(autograd, name)
+    raise AttributeError(f"module {__name__!r} has no attribute {name!r}")

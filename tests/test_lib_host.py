@@ -406,3 +406,12 @@ def test_plan_load_rejects_bad_files_without_a_gpu(fio, tmp_path):
     assert lib.fio_plan_load(os.fsencode(good_mode), 0, ctypes.byref(h)) == fio.FIO_EINVAL
     assert not h.value
     assert b"host tables" in lib.fio_last_error()
+
+
+def test_autograd_functions_reachable_from_fio(fio):
+    """fio.FIOApply / fio.FIOAdjoint are the autograd functions (imported on use)."""
+    pytest.importorskip("torch")
+    from paper_math_0610051_gb300 import autograd
+    assert fio.FIOApply is autograd.FIOApply and fio.FIOAdjoint is autograd.FIOAdjoint
+    with pytest.raises(AttributeError):
+        fio.no_such_name
